@@ -1,0 +1,263 @@
+"""Pins for the CPU oracle against facts fixed by the paper and by mathematics
+(no GPU).  Each test is chosen so that a plausible slip in the oracle (a
+dropped term, a wrong sign or index, a transposed operand) breaks it."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from problems import cd, configs
+
+EPS = np.finfo(np.float64).eps
+
+
+def _random_csr(n, seed, density=0.3, zero_row=None):
+    rs = np.random.default_rng(seed)
+    A = rs.uniform(-1, 1, (n, n)) * (rs.uniform(size=(n, n)) < density)
+    A += np.diag(rs.uniform(2, 3, n) * n * density)
+    if zero_row is not None:
+        A[zero_row] = 0.0
+    rowptr = np.zeros(n + 1, dtype=np.int32)
+    cols, vals = [], []
+    for i in range(n):
+        nz = np.nonzero(A[i])[0]
+        cols.extend(nz)
+        vals.extend(A[i, nz])
+        rowptr[i + 1] = len(cols)
+    return A, rowptr, np.array(cols, dtype=np.int32), np.array(vals)
+
+
+# ------------------------------------------------------------------ GS(p)
+@pytest.mark.parametrize("p", [1.0, 2.0, math.inf, 3.5])
+def test_gs_rows_have_unit_norm(p):
+    """Sec. 1: after GS(p) every row has unit L_p norm."""
+    s = configs.c1()
+    val, b, d = oracle.gs_scale(s.rowptr, s.colidx, s.val, s.b, p)
+    for i in range(0, s.n, 7):
+        row = val[s.rowptr[i]:s.rowptr[i + 1]]
+        assert abs(oracle.lp_norm_def(row, p) - 1.0) <= 8 * EPS
+
+
+def test_gs_closed_form_rows():
+    rowptr = np.array([0, 2], dtype=np.int32)
+    colidx = np.array([0, 1], dtype=np.int32)
+    for p, want in [(2.0, [0.6, -0.8]), (1.0, [3 / 7, -4 / 7]), (math.inf, [0.75, -1.0])]:
+        val, b, d = oracle.gs_scale(rowptr, colidx, np.array([3.0, -4.0]), np.array([10.0]), p)
+        assert np.allclose(val, want, rtol=2 * EPS, atol=0)
+        assert np.isclose(b[0], 10.0 * d[0], rtol=2 * EPS)
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0, math.inf, 3.5])
+def test_gs_invariant_under_row_scaling(p):
+    """GS(p)(Lambda A) = sign(Lambda) GS(p)(A) for any nonzero diagonal Lambda."""
+    s = configs.c1()
+    rs = np.random.default_rng(1)
+    lam = 10.0 ** rs.uniform(-6, 6, s.n) * np.where(rs.uniform(size=s.n) < 0.3, -1, 1)
+    rows = np.repeat(np.arange(s.n), np.diff(s.rowptr))
+    v1, b1, _ = oracle.gs_scale(s.rowptr, s.colidx, s.val, s.b, p)
+    v2, b2, _ = oracle.gs_scale(s.rowptr, s.colidx, s.val * lam[rows], s.b * lam, p)
+    sg = np.sign(lam)
+    assert np.allclose(v2, sg[rows] * v1, rtol=8 * EPS, atol=0)
+    assert np.allclose(b2, sg * b1, rtol=8 * EPS, atol=1e-300)
+
+
+def test_gs_power_of_two_scaling_is_exact_even_near_overflow():
+    """Scaling a row by 2^k is exact in binary floating point, so GS must give
+    bit-identical output for rows of size ~1e300 (no overflow of |a|^p)."""
+    s = configs.c1()
+    rows = np.repeat(np.arange(s.n), np.diff(s.rowptr))
+    k = np.where(np.arange(s.n) % 2 == 0, 990, -990)
+    for p in [1.0, 2.0, math.inf, 3.5]:
+        v1, _, _ = oracle.gs_scale(s.rowptr, s.colidx, s.val, None, p)
+        v2, _, _ = oracle.gs_scale(s.rowptr, s.colidx, np.ldexp(s.val, k[rows]), None, p)
+        assert np.array_equal(v1, v2)
+
+
+def test_gs_norm_inequalities():
+    s = configs.c2(10)
+    _, _, d1 = oracle.gs_scale(s.rowptr, s.colidx, s.val, None, 1.0)
+    _, _, d2 = oracle.gs_scale(s.rowptr, s.colidx, s.val, None, 2.0)
+    _, _, di = oracle.gs_scale(s.rowptr, s.colidx, s.val, None, math.inf)
+    nnz = np.diff(s.rowptr)
+    n1, n2, ni = 1 / d1, 1 / d2, 1 / di
+    assert np.all(ni <= n2 * (1 + 4 * EPS)) and np.all(n2 <= n1 * (1 + 4 * EPS))
+    assert np.all(n1 <= nnz * ni * (1 + 4 * EPS))
+
+
+def test_gs_same_solution_dense():
+    """Eq. (2): DAx = Db has the solution of Ax = b."""
+    s = configs.c1(12)
+    x0 = np.linalg.solve(s.dense(), s.b)
+    val, b, _ = oracle.gs_scale(s.rowptr, s.colidx, s.val, s.b, 2.0)
+    sc = cd.System(s.n, s.rowptr, s.colidx, val, b)
+    x1 = np.linalg.solve(sc.dense(), b)
+    assert np.allclose(x0, x1, rtol=1e-12, atol=1e-12)
+    assert np.allclose(x0, s.x_true, rtol=0, atol=1e-10)
+
+
+def test_gs_errors():
+    A, rp, ci, va = _random_csr(6, 0, zero_row=3)
+    with pytest.raises(oracle.OracleError, match="zero row"):
+        oracle.gs_scale(rp, ci, va, None, 2.0)
+    A, rp, ci, va = _random_csr(6, 0)
+    va[2] = np.nan
+    with pytest.raises(oracle.OracleError, match="non-finite"):
+        oracle.gs_scale(rp, ci, va, None, 2.0)
+    with pytest.raises(oracle.OracleError):
+        oracle.gs_scale(rp, ci, np.abs(va), None, 0.5)
+
+
+# ------------------------------------------------------------------ SpMV
+def test_spmv_matches_dense():
+    A, rp, ci, va = _random_csr(37, 3)
+    x = np.random.default_rng(4).normal(size=37)
+    assert np.allclose(oracle.spmv(rp, ci, va, x), A @ x, rtol=1e-14, atol=1e-13)
+
+
+def test_metric_weights_are_gs2_scales():
+    s = configs.c1(8)
+    w = oracle.metric_weights(s.rowptr, s.val)
+    A = s.dense()
+    assert np.allclose(w, 1 / np.sqrt((A**2).sum(1)), rtol=4 * EPS)
+
+
+# ---------------------------------------------------------------- Arnoldi
+def test_arnoldi_relation_and_orthogonality():
+    s = configs.c1(10)
+    A = s.dense()
+    v0 = np.random.default_rng(5).normal(size=s.n)
+    k = 12
+    V, H, steps = oracle.arnoldi(s.rowptr, s.colidx, s.val, v0, k)
+    assert steps == k
+    assert np.abs(A @ V[:, :k] - V @ H).max() <= 1e-12 * np.abs(A).sum(1).max()
+    assert np.abs(np.eye(k + 1) - V.T @ V).max() <= 1e-13
+    assert np.allclose(V[:, 0], v0 / np.linalg.norm(v0), rtol=1e-15, atol=1e-16)
+    assert np.allclose(np.tril(H, -2), 0.0)  # Hessenberg
+    assert np.all(np.diag(H, -1) > 0)
+
+
+# ------------------------------------------------------------------ GMRES
+def _diag_csr(d):
+    n = len(d)
+    return np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.asarray(d, dtype=np.float64)
+
+
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_gmres_finite_termination_on_k_distinct_eigenvalues(k):
+    """A diagonal matrix with k distinct eigenvalues has a grade-k Krylov space:
+    GMRES(m >= k) converges in exactly k steps (to rounding)."""
+    n = 60
+    vals = np.array([1.0 + 0.7 * j for j in range(k)])
+    d = vals[np.arange(n) % k]
+    rp, ci, va = _diag_csr(d)
+    b = np.random.default_rng(6).uniform(1, 2, n)
+    x, info = oracle.gmres(rp, ci, va, b, m=10, tol=1e-12, w=np.ones(n))
+    assert info["conv"] == oracle.CONVERGED
+    assert info["iters"] == k
+    assert np.allclose(x, b / d, rtol=1e-11)
+
+
+def test_gmres_full_equals_dense_lu():
+    A, rp, ci, va = _random_csr(25, 7, density=0.4)
+    b = np.random.default_rng(8).normal(size=25)
+    x, info = oracle.gmres(rp, ci, va, b, m=25, tol=1e-13, w=np.ones(25))
+    assert info["conv"] == oracle.CONVERGED and info["restarts"] == 0
+    assert np.allclose(x, oracle.dense_solve(A, b), rtol=1e-10, atol=1e-12)
+
+
+def test_gmres_estimate_monotone_and_matches_true_residual():
+    s = configs.c1()
+    val, b, _ = oracle.gs_scale(s.rowptr, s.colidx, s.val, s.b, 2.0)
+    n = s.n
+    x, info, hist = oracle.gmres(s.rowptr, s.colidx, val, b, m=40, tol=1e-9, maxit=40,
+                                 w=np.ones(n), history=True)
+    # within one cycle the least-squares residual never increases
+    assert np.all(np.diff(hist) <= 1e-15)
+    r = b - oracle.spmv(s.rowptr, s.colidx, val, x)
+    true = np.linalg.norm(r) / np.linalg.norm(b)
+    assert abs(true - hist[-1]) <= 1e-10 * max(true, 1e-300) + 1e-14
+    assert abs(info["relres_true"] - true) <= 1e-13
+
+
+def test_gmres_restarted_reaches_tolerance_and_reports_metric():
+    s = configs.c1(16)
+    val, b, _ = oracle.gs_scale(s.rowptr, s.colidx, s.val, s.b, 2.0)
+    x, info = oracle.gmres(s.rowptr, s.colidx, val, b, m=20, tol=1e-8)
+    assert info["conv"] == oracle.CONVERGED
+    assert info["restarts"] >= 1
+    assert info["relres_true"] < 1e-8
+    assert abs(oracle.relres(s.rowptr, s.colidx, val, b, x) - info["relres_true"]) < 1e-15
+    # forward error is bounded by cond(A) times the relative residual
+    sc = cd.System(s.n, s.rowptr, s.colidx, val, b)
+    kappa = np.linalg.cond(sc.dense())
+    assert np.linalg.norm(x - s.x_true) / np.linalg.norm(s.x_true) <= 2 * kappa * info["relres_true"]
+
+
+def test_gmres_maxit_is_respected():
+    s = configs.c1()
+    x, info = oracle.gmres(s.rowptr, s.colidx, s.val, s.b, m=20, tol=1e-12, maxit=55)
+    assert info["iters"] == 55 and info["conv"] == oracle.MAXIT
+
+
+# -------------------------------------------------------------- Bi-CGSTAB
+def test_bicgstab_scalar_multiple_of_identity_one_iteration():
+    n = 40
+    rp, ci, va = _diag_csr(np.full(n, 3.5))
+    b = np.random.default_rng(9).normal(size=n)
+    x, info = oracle.bicgstab(rp, ci, va, b, tol=1e-12)
+    assert info["conv"] == oracle.CONVERGED and info["iters"] == 1
+    assert np.allclose(x, b / 3.5, rtol=1e-15)
+
+
+@pytest.mark.parametrize("N", [4, 7, 12])
+def test_bicgstab_matches_dense_lu_on_small_grids(N):
+    s = configs.c1(N)
+    A = s.dense()
+    val, b, _ = oracle.gs_scale(s.rowptr, s.colidx, s.val, s.b, 2.0)
+    x, info = oracle.bicgstab(s.rowptr, s.colidx, val, b, tol=1e-12)
+    assert info["conv"] == oracle.CONVERGED
+    xd = oracle.dense_solve(A, s.b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
+
+
+def test_bicgstab_recovers_manufactured_solution_c1():
+    s = configs.c1()
+    val, b, _ = oracle.gs_scale(s.rowptr, s.colidx, s.val, s.b, 2.0)
+    x, info = oracle.bicgstab(s.rowptr, s.colidx, val, b, tol=1e-8)
+    assert info["conv"] == oracle.CONVERGED and info["relres_true"] < 1e-8
+    sc = cd.System(s.n, s.rowptr, s.colidx, val, b)
+    kappa = np.linalg.cond(sc.dense())
+    assert np.linalg.norm(x - s.x_true) / np.linalg.norm(s.x_true) <= 2 * kappa * info["relres_true"]
+    assert abs(oracle.relres(s.rowptr, s.colidx, val, b, x) - info["relres_true"]) < 1e-15
+
+
+def test_bicgstab_history_and_scaling_helps_c1():
+    """GS(2) cuts the Bi-CGSTAB iteration count on the discontinuous C1 system
+    (the effect reported throughout Sec. 3-6)."""
+    s = configs.c1()
+    _, i0 = oracle.bicgstab(s.rowptr, s.colidx, s.val, s.b, tol=1e-8)
+    val, b, _ = oracle.gs_scale(s.rowptr, s.colidx, s.val, s.b, 2.0)
+    _, i2 = oracle.bicgstab(s.rowptr, s.colidx, val, b, tol=1e-8)
+    assert i2["conv"] == oracle.CONVERGED
+    assert i2["iters"] * 4 < i0["iters"]
+
+
+def test_metric_is_the_gs2_scaled_residual_whatever_the_scaling():
+    """Sec. 2.2: the test is made on the GS(2)-scaled system.  The metric of a
+    GS(1)-scaled solve must equal the plain residual ratio of the GS(2) system."""
+    s = configs.c1(12)
+    v1, b1, _ = oracle.gs_scale(s.rowptr, s.colidx, s.val, s.b, 1.0)
+    x, info = oracle.bicgstab(s.rowptr, s.colidx, v1, b1, tol=1e-6)
+    v2, b2, _ = oracle.gs_scale(s.rowptr, s.colidx, s.val, s.b, 2.0)
+    r = b2 - oracle.spmv(s.rowptr, s.colidx, v2, x)
+    assert abs(np.linalg.norm(r) / np.linalg.norm(b2) - info["relres_true"]) < 1e-14
+
+
+def test_bicgstab_breakdown_is_reported():
+    # rh = r orthogonal to A r: the rotation [[0, 1], [-1, 0]] gives sigma = 0
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    ci = np.array([1, 0], dtype=np.int32)
+    va = np.array([1.0, -1.0])
+    x, info = oracle.bicgstab(rp, ci, va, np.array([1.0, 0.0]), tol=1e-10)
+    assert info["conv"] == oracle.BREAKDOWN and info["iters"] == 0
