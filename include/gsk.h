@@ -1,0 +1,175 @@
+/*
+ * gsk.h -- C ABI of the GB300 library for geometric scaling (GS(p)) and the
+ * restarted GMRES(m) / Bi-CGSTAB solvers of
+ *   D. Gordon, R. Gordon, "Geometric scaling: a simple preconditioner for
+ *   certain linear systems with discontinuous coefficients" (2009).
+ *
+ * Conventions for every entry point:
+ *  - Matrices are CSR with int32 row pointers and column indices (columns in
+ *    any order within a row, each index in [0, n)), values FP64 or FP32.
+ *  - Every array pointer that names matrix or vector data is a DEVICE pointer
+ *    owned by the caller; the library never frees it.  The library owns only
+ *    the workspace held by a gsk_ctx.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  Work is ordered on that stream.
+ *  - Every kernel bounds-checks the CSR structure it reads (rowptr extents,
+ *    column indices); a malformed matrix yields GSK_ERR_ARG, never an
+ *    out-of-range access.
+ *  - No C++ exception crosses the ABI.  Every call returns a gsk_status; the
+ *    text of the last error of a context is available from gsk_last_error.
+ *  - Non-convergence is not an error: a solve returns GSK_OK with
+ *    info->conv != GSK_CONVERGED (the paper's "no conv.", Sec. 2.2).
+ *  - One context runs one solve at a time: calls that share a context must be
+ *    issued on the same stream (or be serialised by the caller).  Use one
+ *    context per concurrent stream.
+ */
+#ifndef GSK_H
+#define GSK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GSK_OK = 0,
+  GSK_ERR_ARG = 1,        /* invalid size, pointer, parameter or CSR structure */
+  GSK_ERR_ZERO_ROW = 2,   /* a row of A is all zeros (Sec. 2 assumes none) */
+  GSK_ERR_NONFINITE = 3,  /* NaN or Inf in A or b */
+  GSK_ERR_OOM = 4,        /* workspace allocation failed */
+  GSK_ERR_CUDA = 5,       /* a CUDA runtime call failed (see gsk_last_error) */
+  GSK_ERR_TIMEOUT = 6     /* a bounded device-side wait gave up */
+} gsk_status;
+
+typedef enum { GSK_F64 = 0, GSK_F32 = 1 } gsk_dtype;
+
+typedef enum {
+  GSK_CONVERGED = 0,  /* the stopping metric fell below tol */
+  GSK_MAXIT = 1,      /* the iteration cap was reached first */
+  GSK_BREAKDOWN = 2,  /* a Bi-CGSTAB breakdown test fired (Sec. 2.2) */
+  GSK_STAGNATED = 3   /* the recursive residual met tol, the true one did not */
+} gsk_conv;
+
+typedef enum {
+  GSK_METRIC_GS2 = 0,   /* Sec. 2.2: ||W(b-Ax)||/||W(b-Ax0)||, W = GS(2) scales of A */
+  GSK_METRIC_PLAIN = 1  /* ||b-Ax||/||b-Ax0|| of the system as given */
+} gsk_metric;
+
+typedef enum {
+  GSK_PREC_F64 = 0,   /* every vector and product in FP64 */
+  GSK_PREC_MIXED = 1  /* FP32 inner Krylov solves inside FP64 iterative refinement */
+} gsk_precision;
+
+typedef struct gsk_ctx gsk_ctx;
+
+/* A sparse n x n matrix.  rowptr has n+1 entries with rowptr[0] = 0 and
+ * rowptr[n] = nnz, non-decreasing; colidx and val have nnz entries. */
+typedef struct {
+  int32_t n;
+  int32_t nnz;
+  const int32_t* rowptr; /* device [n+1] */
+  const int32_t* colidx; /* device [nnz] */
+  void* val;             /* device [nnz], FP64 or FP32 per dtype */
+  int32_t dtype;         /* gsk_dtype */
+} gsk_csr;
+
+/* Solver options; gsk_opts_default() fills the paper's settings. */
+typedef struct {
+  int32_t maxit;          /* iteration cap, default 10000 (Sec. 2.2) */
+  int32_t refresh;        /* Bi-CGSTAB: true-residual restarts allowed after
+                             the recursive residual met tol, default 3 */
+  int32_t precision;      /* gsk_precision, default GSK_PREC_F64 */
+  int32_t metric;         /* gsk_metric, default GSK_METRIC_GS2 */
+  const double* weights;  /* optional device [n] metric weights W (overrides
+                             metric); NULL = derive them from `metric` */
+  double inner_tol;       /* mixed precision: relative tolerance of each FP32
+                             inner solve, default 1e-5 */
+  int32_t inner_maxit;    /* mixed precision: steps per inner solve, default 3*m
+                             (GMRES) or 300 (Bi-CGSTAB) */
+  int32_t max_refinements;/* mixed precision: outer FP64 steps, default 50 */
+} gsk_opts;
+
+/* Result of a solve (host memory). */
+typedef struct {
+  int32_t iters;        /* GMRES: Arnoldi steps over all cycles; Bi-CGSTAB:
+                           iterations (two products by A each); for mixed
+                           precision the sum over inner solves */
+  int32_t restarts;     /* GMRES cycles after the first */
+  int32_t refreshes;    /* Bi-CGSTAB true-residual restarts taken */
+  int32_t refinements;  /* mixed precision: outer FP64 steps */
+  int32_t conv;         /* gsk_conv */
+  double relres_true;   /* metric of the returned x, from a true residual */
+  double relres_rec;    /* last recursive / least-squares estimate seen */
+  float ms;             /* device time of the solve (CUDA events) */
+} gsk_info;
+
+/* Library version string. */
+const char* gsk_version(void);
+
+/* Create a context on `device` (owns workspace, cached graphs, streams). */
+gsk_status gsk_ctx_create(gsk_ctx** ctx, int device);
+/* Destroy a context and free its workspace; NULL is accepted. */
+gsk_status gsk_ctx_destroy(gsk_ctx* ctx);
+/* Text describing the last error on this context ("" if none). */
+const char* gsk_last_error(gsk_ctx* ctx);
+
+/* Default options: maxit 10000, refresh 3, FP64, GS(2) metric. */
+void gsk_opts_default(gsk_opts* opts);
+
+/*
+ * gs_scale -- geometric scaling GS(p) (Sec. 1; Sec. 2, Eq. (2)).
+ * Divides row i of A, and b_i, by ||a_i||_p, the L_p norm of the row's
+ * coefficients (sum |a_ij|^p)^(1/p); p = INFINITY gives max_j |a_ij|.
+ * Afterwards every row of A has unit L_p norm; the solution is unchanged.
+ *   A      in/out: values scaled in place (FP64 or FP32)
+ *   b      in/out: device [n], same dtype as A, scaled in place; may be NULL
+ *   p      >= 1, or INFINITY
+ *   d_out  optional device FP64 [n]: receives d_i = 1/||a_i||_p (the diagonal
+ *          of D); NULL to skip
+ * Errors: GSK_ERR_ARG (p < 1, bad sizes/pointers), GSK_ERR_ZERO_ROW,
+ * GSK_ERR_NONFINITE.  On error A and b are left unmodified.
+ * Synchronises `stream` to read the error flags back.
+ */
+gsk_status gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, void* stream);
+
+/*
+ * gsk_spmv -- y = A x, the product every Krylov step performs (Sec. 2).
+ *   x, y   device [n] of A's dtype; x and y must not overlap.
+ * Asynchronous on `stream`.
+ */
+gsk_status gsk_spmv(gsk_ctx* ctx, const gsk_csr* A, const void* x, void* y, void* stream);
+
+/*
+ * gmres_solve -- restarted GMRES(m) with classical Gram-Schmidt applied twice
+ * (Sec. 2) on the system as given (apply gs_scale first for GS).
+ *   b      device [n], A's dtype
+ *   x      in: initial guess x0 (zeros = the paper's u0 = 0, Sec. 2.1);
+ *          out: solution.  Device [n], A's dtype.
+ *   m      Krylov dimension per cycle, 1..256
+ *   tol    stop when ||W(b-Ax)||/||W(b-Ax0)|| < tol (Sec. 2.2)
+ *   opts   NULL for defaults
+ *   info   host pointer or NULL; when non-NULL the call synchronises `stream`
+ *          and fills it.
+ * The whole solve runs on the device: no host round trip per iteration.
+ */
+gsk_status gmres_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, int m, double tol,
+                       const gsk_opts* opts, gsk_info* info, void* stream);
+
+/*
+ * bicgstab_solve -- Bi-CGSTAB (Sec. 2; van der Vorst 1992) with breakdown
+ * tolerance 1e-16 * DBL_EPSILON relative to the vector norms (Sec. 2.2) and
+ * true-residual confirmation.  Arguments as for gmres_solve.
+ */
+gsk_status bicgstab_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, double tol,
+                          const gsk_opts* opts, gsk_info* info, void* stream);
+
+/* Device workspace a solve of this shape needs (solver: 0 = GMRES, 1 =
+ * Bi-CGSTAB), so that callers can budget HBM before admitting work. */
+gsk_status gsk_workspace_bytes(int n, int nnz, int solver, int m, int precision, size_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSK_H */

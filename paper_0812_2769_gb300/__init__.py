@@ -1,0 +1,258 @@
+"""Python binding of libgsk: geometric scaling GS(p) with restarted GMRES(m)
+and Bi-CGSTAB on GB300 (sm_103a).
+
+This module only marshals arguments to the C ABI declared in
+``include/gsk.h``: torch tensors supply device memory and streams, and every
+step of the computation runs in the library's CUDA kernels.  There is no CPU
+path: if ``libgsk.so`` has not been built, loading raises.
+
+Typical use::
+
+    import torch, paper_0812_2769_gb300 as gsk
+    A = gsk.Csr.from_host(rowptr, colidx, val, device="cuda")
+    b = torch.as_tensor(rhs, device="cuda")
+    gsk.gs_scale(A, b, p=2.0)                 # Sec. 2, Eq. (2)
+    x = torch.zeros_like(b)
+    info = gsk.bicgstab_solve(A, b, x, tol=1e-8)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgsk.so")
+
+OK, ERR_ARG, ERR_ZERO_ROW, ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT = range(7)
+F64, F32 = 0, 1
+CONVERGED, MAXIT, BREAKDOWN, STAGNATED = 0, 1, 2, 3
+CONV_NAMES = {0: "converged", 1: "maxit", 2: "breakdown", 3: "stagnated"}
+METRIC_GS2, METRIC_PLAIN = 0, 1
+PREC_F64, PREC_MIXED = 0, 1
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_ZERO_ROW", 3: "ERR_NONFINITE", 4: "ERR_OOM", 5: "ERR_CUDA",
+                6: "ERR_TIMEOUT"}
+
+
+class GskError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CsrC(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("rowptr", C.c_void_p), ("colidx", C.c_void_p),
+                ("val", C.c_void_p), ("dtype", C.c_int32)]
+
+
+class OptsC(C.Structure):
+    _fields_ = [("maxit", C.c_int32), ("refresh", C.c_int32), ("precision", C.c_int32), ("metric", C.c_int32),
+                ("weights", C.c_void_p), ("inner_tol", C.c_double), ("inner_maxit", C.c_int32),
+                ("max_refinements", C.c_int32)]
+
+
+class InfoC(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("refreshes", C.c_int32),
+                ("refinements", C.c_int32), ("conv", C.c_int32), ("relres_true", C.c_double),
+                ("relres_rec", C.c_double), ("ms", C.c_float)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["conv_name"] = CONV_NAMES.get(self.conv, str(self.conv))
+        return d
+
+
+_lib = None
+
+# every entry point of include/gsk.h, with its ctypes signature
+SIGNATURES = {
+    "gsk_version": ([], C.c_char_p),
+    "gsk_ctx_create": ([C.POINTER(C.c_void_p), C.c_int], C.c_int),
+    "gsk_ctx_destroy": ([C.c_void_p], C.c_int),
+    "gsk_last_error": ([C.c_void_p], C.c_char_p),
+    "gsk_opts_default": ([C.POINTER(OptsC)], None),
+    "gs_scale": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p], C.c_int),
+    "gsk_spmv": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "gmres_solve": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                     C.POINTER(OptsC), C.POINTER(InfoC), C.c_void_p], C.c_int),
+    "bicgstab_solve": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_double,
+                        C.POINTER(OptsC), C.POINTER(InfoC), C.c_void_p], C.c_int),
+    "gsk_workspace_bytes": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+}
+
+
+def lib():
+    """Load libgsk.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_0812_2769_gb300.build` "
+                              "(or __graft_entry__.build()); there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def version() -> str:
+    return lib().gsk_version().decode()
+
+
+class Context:
+    """A library context on one CUDA device (workspace, cached graphs)."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self._h = C.c_void_p()
+        st = lib().gsk_ctx_create(C.byref(self._h), device)
+        if st != OK:
+            raise GskError(st, "gsk_ctx_create failed")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def last_error(self) -> str:
+        return lib().gsk_last_error(self._h).decode()
+
+    def check(self, st: int):
+        if st != OK:
+            raise GskError(st, self.last_error())
+
+    def close(self):
+        if self._h:
+            lib().gsk_ctx_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default_ctx: dict[int, Context] = {}
+
+
+def default_context(device: int = 0) -> Context:
+    if device not in _default_ctx:
+        _default_ctx[device] = Context(device)
+    return _default_ctx[device]
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+@dataclass
+class Csr:
+    """A device CSR matrix held in torch tensors (int32 indices)."""
+
+    rowptr: object
+    colidx: object
+    val: object
+
+    @property
+    def n(self) -> int:
+        return int(self.rowptr.numel()) - 1
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colidx.numel())
+
+    @property
+    def dtype(self) -> int:
+        return F64 if self.val.dtype == _torch().float64 else F32
+
+    @classmethod
+    def from_host(cls, rowptr, colidx, val, device="cuda", dtype=None):
+        torch = _torch()
+        val_t = torch.as_tensor(val)
+        if dtype is not None:
+            val_t = val_t.to(dtype)
+        return cls(torch.as_tensor(rowptr, dtype=torch.int32).to(device).contiguous(),
+                   torch.as_tensor(colidx, dtype=torch.int32).to(device).contiguous(),
+                   val_t.to(device).contiguous())
+
+    def c(self) -> CsrC:
+        return CsrC(self.n, self.nnz, self.rowptr.data_ptr(), self.colidx.data_ptr(), self.val.data_ptr(),
+                    self.dtype)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return C.c_void_p(_torch().cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def opts(maxit=10000, refresh=3, precision=PREC_F64, metric=METRIC_GS2, weights=None, inner_tol=1e-5,
+         inner_maxit=0, max_refinements=50) -> OptsC:
+    o = OptsC()
+    lib().gsk_opts_default(C.byref(o))
+    o.maxit, o.refresh, o.precision, o.metric = maxit, refresh, precision, metric
+    o.weights = None if weights is None else weights.data_ptr()
+    o.inner_tol, o.inner_maxit, o.max_refinements = inner_tol, inner_maxit, max_refinements
+    return o
+
+
+def gs_scale(A: Csr, b=None, p: float = 2.0, d_out=None, ctx: Context | None = None, stream=None):
+    """GS(p) in place on A (and b): row i divided by ||a_i||_p (Sec. 2, Eq. (2))."""
+    ctx = ctx or default_context(A.val.device.index or 0)
+    Ac = A.c()
+    ctx.check(lib().gs_scale(ctx.handle, C.byref(Ac), _ptr(b), float(p), _ptr(d_out), _stream_ptr(stream)))
+    return d_out
+
+
+def gsk_spmv(A: Csr, x, y, ctx: Context | None = None, stream=None):
+    """y = A x on the device."""
+    ctx = ctx or default_context(A.val.device.index or 0)
+    Ac = A.c()
+    ctx.check(lib().gsk_spmv(ctx.handle, C.byref(Ac), _ptr(x), _ptr(y), _stream_ptr(stream)))
+    return y
+
+
+def gmres_solve(A: Csr, b, x, m: int = 30, tol: float = 1e-8, options: OptsC | None = None,
+                ctx: Context | None = None, stream=None, sync: bool = True):
+    """Restarted GMRES(m) with CGS2 (Sec. 2); x holds x0 on entry, the solution on exit."""
+    ctx = ctx or default_context(A.val.device.index or 0)
+    Ac = A.c()
+    info = InfoC()
+    o = options if options is not None else opts()
+    ctx.check(lib().gmres_solve(ctx.handle, C.byref(Ac), _ptr(b), _ptr(x), int(m), float(tol), C.byref(o),
+                                C.byref(info) if sync else None, _stream_ptr(stream)))
+    return info.as_dict() if sync else None
+
+
+def bicgstab_solve(A: Csr, b, x, tol: float = 1e-8, options: OptsC | None = None, ctx: Context | None = None,
+                   stream=None, sync: bool = True):
+    """Bi-CGSTAB (Sec. 2); x holds x0 on entry, the solution on exit."""
+    ctx = ctx or default_context(A.val.device.index or 0)
+    Ac = A.c()
+    info = InfoC()
+    o = options if options is not None else opts()
+    ctx.check(lib().bicgstab_solve(ctx.handle, C.byref(Ac), _ptr(b), _ptr(x), float(tol), C.byref(o),
+                                   C.byref(info) if sync else None, _stream_ptr(stream)))
+    return info.as_dict() if sync else None
+
+
+def workspace_bytes(n: int, nnz: int, solver: str = "bicgstab", m: int = 30, precision: int = PREC_F64) -> int:
+    out = C.c_size_t()
+    st = lib().gsk_workspace_bytes(n, nnz, 0 if solver == "gmres" else 1, m, precision, C.byref(out))
+    if st != OK:
+        raise GskError(st, "gsk_workspace_bytes")
+    return int(out.value)
+
+
+INF = math.inf

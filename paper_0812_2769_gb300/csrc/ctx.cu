@@ -1,0 +1,148 @@
+// Context management and the thin C ABI entry points that are not solvers.
+#include <cmath>
+
+#include "internal.hpp"
+
+gsk_status gsk_ctx::reserve(size_t bytes) {
+  if (bytes <= ws_bytes) return GSK_OK;
+  clear_graphs();
+  if (ws) {
+    cudaError_t e = cudaFree(ws);
+    ws = nullptr;
+    ws_bytes = 0;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFree(workspace)");
+  }
+  size_t want = bytes + bytes / 8 + (1u << 20);
+  cudaError_t e = cudaMalloc(&ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ws = nullptr;
+    return fail(GSK_ERR_OOM, "workspace allocation of " + std::to_string(want) + " bytes failed");
+  }
+  // reduction counters and flags must start at zero
+  e = cudaMemset(ws, 0, want);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(workspace)");
+  ws_bytes = want;
+  return GSK_OK;
+}
+
+void gsk_ctx::clear_graphs() {
+  for (auto& g : graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  graphs.clear();
+}
+
+gsk::GraphEntry* gsk_ctx::find_graph(const std::vector<uint64_t>& key) {
+  for (auto& g : graphs)
+    if (g.key == key) {
+      g.last_use = ++clock;
+      return &g;
+    }
+  return nullptr;
+}
+
+gsk::GraphEntry* gsk_ctx::add_graph(const std::vector<uint64_t>& key, cudaGraphExec_t exec) {
+  constexpr size_t kMaxGraphs = 16;
+  if (graphs.size() >= kMaxGraphs) {
+    size_t victim = 0;
+    for (size_t i = 1; i < graphs.size(); ++i)
+      if (graphs[i].last_use < graphs[victim].last_use) victim = i;
+    cudaGraphExecDestroy(graphs[victim].exec);
+    graphs.erase(graphs.begin() + victim);
+  }
+  graphs.push_back(gsk::GraphEntry{key, exec, ++clock});
+  return &graphs.back();
+}
+
+extern "C" {
+
+const char* gsk_version(void) { return "gsk 0.1 (sm_103a)"; }
+
+gsk_status gsk_ctx_create(gsk_ctx** out, int device) {
+  if (!out) return GSK_ERR_ARG;
+  *out = nullptr;
+  gsk_ctx* ctx = new (std::nothrow) gsk_ctx();
+  if (!ctx) return GSK_ERR_OOM;
+  ctx->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->host_pinned, 1 << 16);
+  if (e != cudaSuccess) {
+    gsk_ctx_destroy(ctx);
+    return GSK_ERR_CUDA;
+  }
+  *out = ctx;
+  return GSK_OK;
+}
+
+gsk_status gsk_ctx_destroy(gsk_ctx* ctx) {
+  if (!ctx) return GSK_OK;
+  cudaSetDevice(ctx->device);
+  ctx->clear_graphs();
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+  if (ctx->capture) cudaStreamDestroy(ctx->capture);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  delete ctx;
+  return GSK_OK;
+}
+
+const char* gsk_last_error(gsk_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+void gsk_opts_default(gsk_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->maxit = 10000;
+  o->refresh = 3;
+  o->precision = GSK_PREC_F64;
+  o->metric = GSK_METRIC_GS2;
+  o->weights = nullptr;
+  o->inner_tol = 1e-5;
+  o->inner_maxit = 0;
+  o->max_refinements = 50;
+}
+
+gsk_status gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, void* stream) {
+  if (!ctx) return GSK_ERR_ARG;
+  gsk_status s = gsk::check_csr(ctx, A);
+  if (s != GSK_OK) return s;
+  if (!(p >= 1.0)) return ctx->fail(GSK_ERR_ARG, "p must be >= 1 or INFINITY");
+  if (A->n == 0) return GSK_OK;
+  return gsk::run_gs_scale(ctx, A, b, p, d_out, (cudaStream_t)stream);
+}
+
+gsk_status gsk_spmv(gsk_ctx* ctx, const gsk_csr* A, const void* x, void* y, void* stream) {
+  if (!ctx) return GSK_ERR_ARG;
+  gsk_status s = gsk::check_csr(ctx, A);
+  if (s != GSK_OK) return s;
+  if (A->n > 0 && (!x || !y)) return ctx->fail(GSK_ERR_ARG, "NULL x or y");
+  if ((s = ctx->reserve(256)) != GSK_OK) return s;
+  // the structure error word lives at the start of the workspace; it is
+  // read back by gsk_spmv_check (tests) and reset here
+  int* err = (int*)ctx->ws;
+  cudaStream_t st = (cudaStream_t)stream;
+  GSK_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+  return gsk::launch_spmv(ctx, A, x, y, err, st);
+}
+
+gsk_status gsk_workspace_bytes(int n, int nnz, int solver, int m, int precision, size_t* bytes) {
+  if (!bytes || n < 0 || nnz < 0) return GSK_ERR_ARG;
+  const size_t nn = (size_t)n;
+  size_t vec = precision == GSK_PREC_MIXED ? 4 : 8;
+  size_t b = 1u << 20;  // states, counters, reduction scratch
+  if (solver == 0) {
+    if (m < 1 || m > gsk::kMaxM) return GSK_ERR_ARG;
+    b += vec * nn * (size_t)(m + 2) + 8 * nn;  // basis, weights
+  } else {
+    b += vec * nn * 6 + 8 * nn;
+  }
+  if (precision == GSK_PREC_MIXED) b += 8 * nn * 2 + 4 * (size_t)nnz;  // FP64 residual/correction + FP32 values
+  *bytes = b;
+  return GSK_OK;
+}
+
+}  // extern "C"

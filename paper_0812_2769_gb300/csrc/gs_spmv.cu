@@ -1,0 +1,240 @@
+// Geometric scaling GS(p) (Sec. 1; Sec. 2, Eq. (2)) and the CSR product
+// y = A x used by every Krylov step.
+//
+// GS(p) runs as two kernels so that a malformed or singular input leaves A
+// and b untouched: gs_norm computes d_i = 1/||a_i||_p for every row and
+// records errors (bad structure, non-finite values, zero rows); gs_apply then
+// multiplies row i of A and b_i by d_i only if no error was recorded.  Both
+// stage each 32-row tile's nonzeros through shared memory so that global
+// loads and stores are coalesced and each lane works on its own row.
+#include "internal.hpp"
+
+namespace gsk {
+
+enum PMode : int { kP1 = 0, kP2 = 1, kPInf = 2, kPGen = 3 };
+
+struct TileExt {
+  int row, rs, re, e0, e1;
+  bool ok, tile_ok;
+};
+
+// Extents of the tile r0..r0+31 and of this lane's row, with bounds checks.
+__device__ __forceinline__ TileExt tile_extents(const int* __restrict__ rowptr, int n, int nnz, int r0,
+                                                int* err) {
+  TileExt t;
+  t.row = r0 + lane_id();
+  const int last = min(31, n - 1 - r0);
+  t.rs = t.re = 0;
+  if (t.row < n) {
+    t.rs = __ldg(rowptr + t.row);
+    t.re = __ldg(rowptr + t.row + 1);
+  }
+  t.e0 = __shfl_sync(kFull, t.rs, 0);
+  t.e1 = __shfl_sync(kFull, t.re, last);
+  t.tile_ok = (t.e0 >= 0) && (t.e1 <= nnz) && (t.e1 >= t.e0);
+  t.ok = t.tile_ok && ((t.row >= n) || (t.rs >= t.e0 && t.re >= t.rs && t.re <= t.e1));
+  if (!t.ok) atomicOr(err, kErrIndex);
+  return t;
+}
+
+// ||a||_p of one row held in shared memory (values converted to double).
+// p = 2 sums squares directly unless the largest magnitude is near the ends
+// of the exponent range, where the row is first scaled by an exact power of
+// two; this is the definition up to rounding.  The largest magnitude and the
+// finiteness test use the integer bit patterns (no FP64 work).
+template <typename T>
+__device__ __forceinline__ double row_norm(const T* v, int len, int pmode, double p, int* err) {
+  unsigned long long mb = 0ull;
+  bool nonfinite = false;
+  for (int k = 0; k < len; ++k) {
+    unsigned long long bits = (unsigned long long)__double_as_longlong((double)v[k]) & 0x7fffffffffffffffull;
+    nonfinite |= bits >= 0x7ff0000000000000ull;
+    mb = bits > mb ? bits : mb;
+  }
+  if (nonfinite) {
+    atomicOr(err, kErrNonFinite);
+    return 1.0;
+  }
+  if (mb == 0ull) {
+    atomicOr(err, kErrZeroRow);
+    return 1.0;
+  }
+  const double m = __longlong_as_double((long long)mb);
+  if (pmode == kPInf) return m;
+  if (pmode == kP1) {
+    double s = 0.0;
+    for (int k = 0; k < len; ++k) s += fabs((double)v[k]);
+    return s;
+  }
+  if (pmode == kP2) {
+    const int e = (int)(mb >> 52) - 1023;
+    if (e > -480 && e < 480) {
+      double s = 0.0;
+      for (int k = 0; k < len; ++k) {
+        const double a = (double)v[k];
+        s = fma(a, a, s);
+      }
+      return sqrt(s);
+    }
+    const double sc = ldexp(1.0, -e), isc = ldexp(1.0, e);
+    double s = 0.0;
+    for (int k = 0; k < len; ++k) {
+      const double a = (double)v[k] * sc;
+      s = fma(a, a, s);
+    }
+    return sqrt(s) * isc;
+  }
+  double s = 0.0;
+  for (int k = 0; k < len; ++k) s += pow(fabs((double)v[k]) / m, p);
+  return m * pow(s, 1.0 / p);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) gs_norm_kernel(int n, int nnz, const int* __restrict__ rowptr,
+                                                         const T* __restrict__ val, const T* __restrict__ b,
+                                                         int pmode, double p, double* __restrict__ d,
+                                                         int* err) {
+  __shared__ T stage[kWarpsPerBlock][kStageCap];
+  T* st = stage[warp_id()];
+  const int ntiles = (n + 31) / 32;
+  for (int tile = blockIdx.x * kWarpsPerBlock + warp_id(); tile < ntiles; tile += gridDim.x * kWarpsPerBlock) {
+    const TileExt t = tile_extents(rowptr, n, nnz, tile * 32, err);
+    const int cnt = t.e1 - t.e0;
+    double nrm = 1.0;
+    if (t.tile_ok && cnt <= kStageCap) {
+      for (int k = lane_id(); k < cnt; k += 32) st[k] = __ldg(val + t.e0 + k);
+      __syncwarp();
+      if (t.ok && t.row < n) nrm = row_norm(st + (t.rs - t.e0), t.re - t.rs, pmode, p, err);
+      __syncwarp();
+    } else if (t.ok && t.row < n) {
+      nrm = row_norm(val + t.rs, t.re - t.rs, pmode, p, err);
+    }
+    if (t.row < n) {
+      d[t.row] = 1.0 / nrm;
+      if (b) {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong((double)b[t.row]);
+        if ((bits & 0x7ff0000000000000ull) == 0x7ff0000000000000ull) atomicOr(err, kErrNonFinite);
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) gs_apply_kernel(int n, int nnz, const int* __restrict__ rowptr,
+                                                          T* __restrict__ val, T* __restrict__ b,
+                                                          const double* __restrict__ d, int* err) {
+  if (*(volatile int*)err != 0) return;  // errors found by gs_norm: leave A and b as they are
+  __shared__ T stage[kWarpsPerBlock][kStageCap];
+  T* st = stage[warp_id()];
+  const int ntiles = (n + 31) / 32;
+  for (int tile = blockIdx.x * kWarpsPerBlock + warp_id(); tile < ntiles; tile += gridDim.x * kWarpsPerBlock) {
+    const TileExt t = tile_extents(rowptr, n, nnz, tile * 32, err);
+    const int cnt = t.e1 - t.e0;
+    const double di = t.row < n ? d[t.row] : 0.0;
+    if (cnt <= kStageCap) {
+      for (int k = lane_id(); k < cnt; k += 32) st[k] = val[t.e0 + k];
+      __syncwarp();
+      if (t.row < n)
+        for (int k = t.rs - t.e0; k < t.re - t.e0; ++k) st[k] = (T)((double)st[k] * di);
+      __syncwarp();
+      for (int k = lane_id(); k < cnt; k += 32) val[t.e0 + k] = st[k];
+      __syncwarp();
+    } else if (t.row < n) {
+      for (int k = t.rs; k < t.re; ++k) val[k] = (T)((double)val[k] * di);
+    }
+    if (b && t.row < n) b[t.row] = (T)((double)b[t.row] * di);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) spmv_kernel(int n, int nnz, const int* __restrict__ rowptr,
+                                                      const int* __restrict__ colidx, const T* __restrict__ val,
+                                                      const T* __restrict__ x, T* __restrict__ y, int* err) {
+  __shared__ TileStage<T, kStageCap> stage[kWarpsPerBlock];
+  const int ntiles = (n + 31) / 32;
+  for (int tile = blockIdx.x * kWarpsPerBlock + warp_id(); tile < ntiles; tile += gridDim.x * kWarpsPerBlock) {
+    const int r0 = tile * 32;
+    const T v = csr_tile_row<T, T, kStageCap>(rowptr, colidx, val, x, n, nnz, r0, stage[warp_id()], err);
+    if (r0 + lane_id() < n) y[r0 + lane_id()] = v;
+  }
+}
+
+// Counts entries of w outside [1 - 4 eps, 1 + 4 eps] (integer compares on
+// the bit patterns of positive doubles) and stores 1 in *out when there are
+// none: the stopping-test weights are then the identity and are not loaded.
+__global__ void __launch_bounds__(kBlock) unit_check_kernel(int n, const double* __restrict__ w, GridRed red,
+                                                            int* out) {
+  __shared__ double sm[4 * kWarpsPerBlock], blk[1], tot[1];
+  const long long lo = __double_as_longlong(1.0 - 4.0 * 2.220446049250313e-16);
+  const long long hi = __double_as_longlong(1.0 + 4.0 * 2.220446049250313e-16);
+  int cnt = 0;
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+    const long long bits = __double_as_longlong(__ldg(w + i));
+    cnt += (bits < lo || bits > hi) ? 1 : 0;
+  }
+  double acc[1] = {(double)cnt};
+  block_sum<1, kBlock>(acc, sm, blk);
+  if (grid_sum(blk, 1, red, tot) && threadIdx.x == 0) *out = tot[0] == 0.0 ? 1 : 0;
+}
+
+void launch_gs_norm(gsk_ctx* ctx, int n, int nnz, const int* rowptr, const double* val, double p, double* d,
+                    int* err, cudaStream_t st) {
+  int pmode = p == 1.0 ? kP1 : (p == 2.0 ? kP2 : (p > 1e300 ? kPInf : kPGen));
+  const int grid = ctx->grid_for((n + 31) / 32, kWarpsPerBlock, 8);
+  gs_norm_kernel<double><<<grid, kBlock, 0, st>>>(n, nnz, rowptr, val, nullptr, pmode, p, d, err);
+}
+
+void launch_unit_check(gsk_ctx* ctx, int n, const double* w, const GridRed& red, int* out, cudaStream_t st) {
+  int grid = ctx->grid_for(n, kBlock, 8);
+  if (grid > red.maxgrid) grid = red.maxgrid;
+  unit_check_kernel<<<grid, kBlock, 0, st>>>(n, w, red, out);
+}
+
+gsk_status launch_spmv(gsk_ctx* ctx, const gsk_csr* A, const void* x, void* y, int* err, cudaStream_t st) {
+  if (A->n == 0) return GSK_OK;
+  const int grid = ctx->grid_for((A->n + 31) / 32, kWarpsPerBlock, 8);
+  if (A->dtype == GSK_F64)
+    spmv_kernel<double><<<grid, kBlock, 0, st>>>(A->n, A->nnz, A->rowptr, A->colidx, (const double*)A->val,
+                                                  (const double*)x, (double*)y, err);
+  else
+    spmv_kernel<float><<<grid, kBlock, 0, st>>>(A->n, A->nnz, A->rowptr, A->colidx, (const float*)A->val,
+                                                 (const float*)x, (float*)y, err);
+  GSK_CK(cudaGetLastError());
+  return GSK_OK;
+}
+
+gsk_status run_gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, cudaStream_t st) {
+  int pmode;
+  if (p == 1.0) pmode = kP1;
+  else if (p == 2.0) pmode = kP2;
+  else if (p > 1e300) pmode = kPInf;
+  else pmode = kPGen;
+  const int n = A->n;
+  // workspace: error word + d (when the caller does not want it)
+  Arena a;
+  a.take<int>(64);
+  if (!d_out) a.take<double>(n);
+  gsk_status s = ctx->reserve(a.off);
+  if (s != GSK_OK) return s;
+  a = Arena{(char*)ctx->ws, ctx->ws_bytes, 0};
+  int* err = a.take<int>(64);
+  double* d = d_out ? d_out : a.take<double>(n);
+  GSK_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+  const int grid = ctx->grid_for((n + 31) / 32, kWarpsPerBlock, 8);
+  if (A->dtype == GSK_F64) {
+    gs_norm_kernel<double><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const double*)A->val,
+                                                     (const double*)b, pmode, p, d, err);
+    gs_apply_kernel<double><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (double*)A->val, (double*)b, d, err);
+  } else {
+    gs_norm_kernel<float><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const float*)A->val,
+                                                    (const float*)b, pmode, p, d, err);
+    gs_apply_kernel<float><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (float*)A->val, (float*)b, d, err);
+  }
+  GSK_CK(cudaGetLastError());
+  int* hbits = (int*)ctx->host_pinned;
+  GSK_CK(cudaMemcpyAsync(hbits, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GSK_CK(cudaStreamSynchronize(st));
+  return err_bits_status(ctx, *hbits);
+}
+
+}  // namespace gsk

@@ -1,0 +1,136 @@
+// Host-side internals of libgsk: the context, its workspace arena, launch
+// geometry and the cache of instantiated CUDA graphs.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gsk.h"
+#include "device_common.cuh"
+
+namespace gsk {
+
+constexpr int kBlock = 256;           // threads per block for every kernel
+constexpr int kWarpsPerBlock = kBlock / 32;
+constexpr int kStageCap = 256;        // nonzeros staged per 32-row tile (7-point: 224)
+constexpr int kMaxRedValues = 72;     // values per grid-reduction site (GMRES: m+2)
+constexpr int kMaxM = 64;             // largest GMRES restart length of the graph path
+
+// One instantiated graph plus the key it was built for.
+struct GraphEntry {
+  std::vector<uint64_t> key;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t last_use = 0;
+};
+
+// Bump allocator over the context's device workspace.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0, off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+}  // namespace gsk
+
+struct gsk_ctx {
+  int device = 0;
+  int num_sms = 0;
+  std::string last_error;
+  // device workspace
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  // pinned host staging for small read-backs
+  void* host_pinned = nullptr;
+  cudaStream_t capture = nullptr;  // private stream used only for graph capture
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<gsk::GraphEntry> graphs;
+  uint64_t clock = 0;
+
+  gsk_status fail(gsk_status st, const std::string& what) {
+    last_error = what;
+    return st;
+  }
+  gsk_status cuda_fail(cudaError_t e, const char* what) {
+    last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return GSK_ERR_CUDA;
+  }
+  // Make the workspace at least `bytes` large.  Growing invalidates every
+  // cached graph (their kernel arguments point into the old workspace).
+  gsk_status reserve(size_t bytes);
+  void clear_graphs();
+  gsk::GraphEntry* find_graph(const std::vector<uint64_t>& key);
+  gsk::GraphEntry* add_graph(const std::vector<uint64_t>& key, cudaGraphExec_t exec);
+  int grid_for(long long work_items, int per_block, int per_sm = 8) const {
+    long long g = (work_items + per_block - 1) / per_block;
+    long long cap = (long long)num_sms * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+  }
+};
+
+#define GSK_CK(call)                                   \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return ctx->cuda_fail(e_, #call); \
+  } while (0)
+
+namespace gsk {
+
+// Reduction scratch for one site sized for `nv` values and `grid` blocks.
+inline GridRed take_red(Arena& a, int grid, int nv) {
+  GridRed r;
+  int ng = (grid + kGroup - 1) / kGroup;
+  r.partials = a.take<double>((size_t)nv * grid);
+  r.gpartials = a.take<double>((size_t)nv * ng);
+  r.counters = a.take<unsigned>(ng + 1);
+  r.maxgrid = grid;
+  return r;
+}
+
+// Validates the host-visible parts of a CSR descriptor.
+inline gsk_status check_csr(gsk_ctx* ctx, const gsk_csr* A) {
+  if (!A) return ctx->fail(GSK_ERR_ARG, "A is NULL");
+  if (A->n < 0 || A->nnz < 0) return ctx->fail(GSK_ERR_ARG, "negative n or nnz");
+  if (A->n > 0 && (!A->rowptr || (A->nnz > 0 && (!A->colidx || !A->val))))
+    return ctx->fail(GSK_ERR_ARG, "NULL rowptr/colidx/val");
+  if (A->dtype != GSK_F64 && A->dtype != GSK_F32) return ctx->fail(GSK_ERR_ARG, "unknown dtype");
+  return GSK_OK;
+}
+
+// Status of the input checks done by the kernels (bits of kErr*).
+inline gsk_status err_bits_status(gsk_ctx* ctx, int bits) {
+  if (bits & kErrIndex) return ctx->fail(GSK_ERR_ARG, "malformed CSR structure (rowptr extent or column index out of range)");
+  if (bits & kErrNonFinite) return ctx->fail(GSK_ERR_NONFINITE, "NaN or Inf in the matrix or right-hand side");
+  if (bits & kErrZeroRow) return ctx->fail(GSK_ERR_ZERO_ROW, "a row of the matrix is all zeros");
+  return GSK_OK;
+}
+
+// launchers implemented in the .cu files (capture-safe: no synchronisation)
+gsk_status launch_spmv(gsk_ctx* ctx, const gsk_csr* A, const void* x, void* y, int* err, cudaStream_t st);
+void launch_gs_norm(gsk_ctx* ctx, int n, int nnz, const int* rowptr, const double* val, double p, double* d,
+                    int* err, cudaStream_t st);
+void launch_unit_check(gsk_ctx* ctx, int n, const double* w, const GridRed& red, int* out, cudaStream_t st);
+gsk_status run_gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, cudaStream_t st);
+
+}  // namespace gsk
+
+// mixed-precision drivers (FP32 inner Krylov, FP64 refinement)
+gsk_status gmres_solve_mixed(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, int m, double tol,
+                             const gsk_opts* opts, gsk_info* info, void* stream);
+gsk_status bicgstab_solve_mixed(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, double tol,
+                                const gsk_opts* opts, gsk_info* info, void* stream);
+
+namespace gsk {
+
+}  // namespace gsk

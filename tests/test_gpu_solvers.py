@@ -1,0 +1,168 @@
+"""GPU parity of the Bi-CGSTAB and GMRES(m) solvers against the CPU oracle,
+through the C ABI.
+
+Parity bar: the same outcome (converged / maxit / breakdown / stagnated),
+iteration counts within 5% (at least +-2), the true metric of the GPU
+solution (recomputed by the oracle) below tol when converged, and the GPU
+solution close to the oracle's: both are tol-accurate solutions of the same
+system, so they may differ by at most about cond(A) * tol; the test uses
+||x_gpu - x_or|| <= max(1e-6, 4 cond_est * tol) ||x_or||.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import gsk, to_dev
+from problems import cd, configs
+
+pytestmark = pytest.mark.gpu
+
+
+def _scaled(sys_, p):
+    if p is None:
+        return sys_
+    val, b, _ = oracle.gs_scale(sys_.rowptr, sys_.colidx, sys_.val, sys_.b, p)
+    return cd.System(sys_.n, sys_.rowptr, sys_.colidx, val, b, sys_.x_true)
+
+
+def _cond_est(sys_):
+    if sys_.n <= 2500:
+        return float(np.linalg.cond(sys_.dense()))
+    return 1e6
+
+
+def _run_gpu(solver, sys_, tol, m=None, maxit=10000, x0=None):
+    import torch
+
+    g = gsk()
+    A, b = to_dev(g, sys_)
+    x = torch.zeros(sys_.n, dtype=torch.float64, device="cuda") if x0 is None else torch.as_tensor(x0, device="cuda")
+    o = g.opts(maxit=maxit)
+    if solver == "gmres":
+        info = g.gmres_solve(A, b, x, m=m, tol=tol, options=o)
+    else:
+        info = g.bicgstab_solve(A, b, x, tol=tol, options=o)
+    return x.cpu().numpy(), info
+
+
+def _compare(solver, sys_, tol, m=None, maxit=10000):
+    x_g, ig = _run_gpu(solver, sys_, tol, m, maxit)
+    if solver == "gmres":
+        x_o, io = oracle.gmres(sys_.rowptr, sys_.colidx, sys_.val, sys_.b, m=m, tol=tol, maxit=maxit)
+    else:
+        x_o, io = oracle.bicgstab(sys_.rowptr, sys_.colidx, sys_.val, sys_.b, tol=tol, maxit=maxit)
+    msg = f"gpu={ig} oracle={io}"
+    assert ig["conv"] == io["conv"], msg
+    assert abs(ig["iters"] - io["iters"]) <= max(2, 0.05 * io["iters"]), msg
+    mu_g = oracle.relres(sys_.rowptr, sys_.colidx, sys_.val, sys_.b, x_g)
+    assert abs(mu_g - ig["relres_true"]) <= 1e-6 * max(mu_g, 1e-300) + 1e-15, (mu_g, msg)
+    if io["conv"] == oracle.CONVERGED:
+        assert mu_g < tol, msg
+        bound = max(1e-6, 4 * _cond_est(sys_) * tol)
+        err = np.linalg.norm(x_g - x_o) / np.linalg.norm(x_o)
+        assert err <= bound, (err, bound, msg)
+    else:
+        # both stopped without reaching tol: the metric reached is comparable
+        assert mu_g <= 10 * max(io["relres_true"], tol) and io["relres_true"] <= 10 * max(mu_g, tol), msg
+    return ig, io
+
+
+@pytest.mark.parametrize("p", [None, 1.0, 2.0, math.inf])
+def test_bicgstab_c1(p):
+    _compare("bicgstab", _scaled(configs.c1(), p), 1e-8)
+
+
+@pytest.mark.parametrize("p", [None, 2.0])
+def test_gmres20_c1_maxit(p):
+    # GMRES(20) stagnates on C1 (the paper's GMRES "converged to ..." rows)
+    _compare("gmres", _scaled(configs.c1(), p), 1e-8, m=20, maxit=600)
+
+
+@pytest.mark.parametrize("m", [5, 16, 30, 40])
+def test_gmres_converges_small_grid(m):
+    _compare("gmres", _scaled(configs.c1(16), 2.0), 1e-8, m=m)
+
+
+def test_gmres_c2_small_gs2():
+    _compare("gmres", _scaled(configs.c2(12), 2.0), 1e-8, m=30)
+
+
+def test_bicgstab_c2_small_all_scalings():
+    s = configs.c2(21)
+    for p in [None, 1.0, 2.0, math.inf]:
+        _compare("bicgstab", _scaled(s, p), 1e-8)
+
+
+def test_bicgstab_random_nonsymmetric():
+    from gpu_util import random_csr
+
+    rp, ci, va = random_csr(3000, 21, min_len=2, max_len=10, long_rows=(7,), long_len=300)
+    b = np.random.default_rng(1).normal(size=3000)
+    _compare("bicgstab", cd.System(3000, rp, ci, va, b), 1e-10)
+
+
+def test_solvers_already_solved_and_maxit_zero():
+    s = _scaled(configs.c1(8), 2.0)
+    x_true = np.linalg.solve(s.dense(), s.b)
+    import torch
+
+    g = gsk()
+    A, b = to_dev(g, s)
+    # x0 = exact solution -> the metric denominator is zero: converged in 0 steps
+    s0 = cd.System(s.n, s.rowptr, s.colidx, s.val, oracle.spmv(s.rowptr, s.colidx, s.val, x_true))
+    A, b = to_dev(g, s0)
+    x = torch.as_tensor(x_true, device="cuda")
+    info = g.bicgstab_solve(A, b, x, tol=1e-8)
+    assert info["iters"] == 0 and info["conv"] == g.CONVERGED
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    info = g.gmres_solve(A, b, x, m=10, tol=1e-8, options=g.opts(maxit=0))
+    assert info["iters"] == 0 and info["conv"] == g.MAXIT
+
+
+def test_bicgstab_breakdown_matches_oracle():
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    ci = np.array([1, 0], dtype=np.int32)
+    va = np.array([1.0, -1.0])
+    s = cd.System(2, rp, ci, va, np.array([1.0, 0.0]))
+    x_g, ig = _run_gpu("bicgstab", s, 1e-10)
+    _, io = oracle.bicgstab(rp, ci, va, s.b, tol=1e-10)
+    assert ig["conv"] == io["conv"] == oracle.BREAKDOWN and ig["iters"] == io["iters"] == 0
+
+
+def test_repeated_solves_are_bitwise_deterministic():
+    import torch
+
+    g = gsk()
+    s = _scaled(configs.c2(16), 2.0)
+    A, b = to_dev(g, s)
+    xs = []
+    for _ in range(3):
+        x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+        g.bicgstab_solve(A, b, x, tol=1e-8)
+        xs.append(x.cpu().numpy())
+        x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+        g.gmres_solve(A, b, x, m=30, tol=1e-8, options=g.opts(maxit=90))
+        xs.append(x.cpu().numpy())
+    assert np.array_equal(xs[0], xs[2]) and np.array_equal(xs[0], xs[4])
+    assert np.array_equal(xs[1], xs[3]) and np.array_equal(xs[1], xs[5])
+
+
+def test_full_c2_bicgstab_gs2_properties():
+    """128^3 (2.1M unknowns): the GPU solution's true metric, recomputed by the
+    oracle in FP64, is below 1e-8, and the manufactured x_true is recovered."""
+    import torch
+
+    g = gsk()
+    s = configs.c2(128)
+    A, b = to_dev(g, s)
+    g.gs_scale(A, b, p=2.0)
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    info = g.bicgstab_solve(A, b, x, tol=1e-8)
+    assert info["conv"] == g.CONVERGED, info
+    xg = x.cpu().numpy()
+    val_s, b_s, _ = oracle.gs_scale(s.rowptr, s.colidx, s.val, s.b, 2.0)
+    mu = oracle.relres(s.rowptr, s.colidx, val_s, b_s, xg)
+    assert mu < 1e-8 and abs(mu - info["relres_true"]) < 1e-6 * mu
+    assert np.linalg.norm(xg - s.x_true) / np.linalg.norm(s.x_true) < 1e-3
