@@ -1,0 +1,463 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GS(p) + Krylov hot path on one GB300.
+
+Workload (one "step"): the 128^3 convection-diffusion system (2,097,152
+unknowns, 14,581,760 nonzeros, 4x4x4 checkerboard a = 1 / 1e4, beta =
+(20, 20, 20), seeded x_true, b = A x_true), freshly copied from a pristine
+device copy, scaled by GS(2) and solved to a relative residual of 1e-8 (the
+GS(2)-scaled metric of Sec. 2.2) twice: with Bi-CGSTAB and with GMRES(30).
+Metric: solves per second (two solves per step).
+
+Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) execute one
+independent replica per GPU (weak scaling, no data-path collective); the
+barrier and the max over ranks only frame the timing.
+
+``--impl reference`` times the CPU oracle on a bounded sample of the same
+workload instead (see cpu_sample()).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solves/sec and SpMV+Krylov HBM GB/s vs peak at rel. residual 1e-8; p50/p99 latency"
+UNIT = "solves/s"
+N_GRID = 128
+TOL = 1e-8
+M_GMRES = 30
+FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of GB300 (measured 1.19 TFLOP/s with an FMA probe)
+SOLVES_PER_STEP = 2
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gsk", choices=["gsk", "reference"])
+    ap.add_argument("--grid", type=int, default=N_GRID, help="grid side (128 = the benchmark workload)")
+    ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel profiling pass")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------- ranks
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def init_dist(world, backend):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value: float) -> float:
+    """Largest value over all ranks (the slowest replica sets the job time)."""
+    if dist is None:
+        return value
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value: float) -> float:
+    if dist is None:
+        return value
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+# ---------------------------------------------------------------- workload
+def workload(grid):
+    from problems import configs
+
+    return configs.c2(grid)
+
+
+def config_dict(s, world):
+    return {"workload": f"3D convection-diffusion {s.meta['N']}^3 (n={s.n}, nnz={s.nnz}), checkerboard 4^3 "
+                        "a=1/1e4, beta=(20,20,20); GS(2) then Bi-CGSTAB and GMRES(30) to rel. residual 1e-8 "
+                        "(GS(2)-scaled metric), FP64",
+            "n": s.n, "nnz": s.nnz, "solves_per_step": SOLVES_PER_STEP, "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (A 183 MB + 8 working vectors of 16.8 MB)"}
+
+
+def kernel_cost(name, step, n, nnz):
+    """Algorithmic (bytes, FP64 flops) of one launch: every operand moved
+    once (CSR int32 indices; x read once per product), no reuse counted."""
+    spmv_b = 12 * nnz + 4 * (n + 1)
+    V = 8 * n
+    k = step + 1 if step is not None and step >= 0 else 1
+    table = {
+        "bcg_init": (spmv_b + 2 * V + 3 * V, 2 * nnz + 4 * n),
+        "bcg_k1_spmv_dot": (spmv_b + 3 * V, 2 * nnz + 4 * n),
+        "bcg_k2a_s_update": (3 * V, 4 * n),
+        "bcg_k2b_spmv_dot": (spmv_b + 2 * V, 2 * nnz + 4 * n),
+        "bcg_k3_xr_update": (7 * V, 10 * n),
+        "bcg_k4_p_update": (4 * V, 4 * n),
+        "bcg_kt_true_residual": (spmv_b + 3 * V, 2 * nnz + 4 * n),
+        "bcg_kr_finish": (4 * V, 0),
+        "gm_init_residual": (spmv_b + 3 * V, 2 * nnz + 4 * n),
+        "gm_gr_restart_residual": (spmv_b + 3 * V, 2 * nnz + 4 * n),
+        "gm_ga_spmv": (spmv_b + 2 * V, 2 * nnz + 3 * n),
+        "gm_gd_cgs_pass1": ((k + 1) * V, 2 * k * n),
+        "gm_gb_cgs_pass2": ((k + 2) * V, 4 * k * n),
+        "gm_gc_cgs_pass3_givens": ((k + 2) * V, 2 * k * n + 2 * n),
+        "gm_gx_x_update": ((k + 2) * V, 2 * k * n),
+        "gs_norm(w)": (8 * nnz + 4 * (n + 1) + V, 2 * nnz),
+        "unit_check": (V, 0),
+    }
+    return table.get(name, (0, 0))
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for d in [os.path.join(ROOT, "paper_0812_2769_gb300", "csrc")]:
+        for fn in sorted(os.listdir(d)):
+            if fn.endswith((".cu", ".cuh", ".hpp")):
+                h.update(open(os.path.join(d, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = source_hash()
+    for ln in open(path):
+        p = ln.split()
+        if len(p) >= 3 and not ln.startswith("#") and p[0] == kernel and p[2] == want:
+            return float(p[1])
+    return None
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    import paper_0812_2769_gb300 as g
+
+    g.lib()
+    dev = torch.device("cuda", local)
+    s = workload(args.grid)
+    val0 = torch.as_tensor(s.val, device=dev)
+    b0 = torch.as_tensor(s.b, device=dev)
+    A = g.Csr.from_host(s.rowptr, s.colidx, s.val, device=dev)
+    b = b0.clone()
+    x1 = torch.zeros(s.n, dtype=torch.float64, device=dev)
+    x2 = torch.zeros_like(x1)
+    ctx = g.Context(local)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        A.val.copy_(val0)
+        b.copy_(b0)
+        g.gs_scale(A, b, p=2.0, ctx=ctx)
+        x1.zero_()
+        i1 = g.bicgstab_solve(A, b, x1, tol=TOL, ctx=ctx)
+        x2.zero_()
+        i2 = g.gmres_solve(A, b, x2, m=M_GMRES, tol=TOL, ctx=ctx)
+        return i1, i2
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    infos = []
+    barrier(dist, local)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        infos.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(dist, local)
+    ms = e0.elapsed_time(e1)
+    t_max = max_over_ranks(dist, ms / 1e3)
+    solves = sum_over_ranks(dist, SOLVES_PER_STEP * args.steps)
+    value = solves / t_max
+
+    # kernels launched in the timed region (per step: 2 for GS(2); each solve
+    # from its counters -- see the launch structure of the two graphs)
+    launches = 0
+    for i1, i2 in infos:
+        checks = i1["refreshes"] + 1
+        launches += 2
+        launches += 3 + 4 * i1["iters"] + (i1["iters"] - checks) + 2 * checks
+        launches += 3 + 4 * i2["iters"] + 3 * (i2["restarts"] + 1)
+    ok = all(i1["conv"] == g.CONVERGED and i2["conv"] == g.CONVERGED and i1["relres_true"] < TOL
+             and i2["relres_true"] < TOL for i1, i2 in infos)
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if True:  # every rank takes part (the max over ranks is a collective)
+        rp_h = torch.as_tensor(s.rowptr).pin_memory()
+        ci_h = torch.as_tensor(s.colidx).pin_memory()
+        va_h = torch.as_tensor(s.val).pin_memory()
+        b_h = torch.as_tensor(s.b).pin_memory()
+        xo1 = torch.empty(s.n, dtype=torch.float64).pin_memory()
+        xo2 = torch.empty_like(xo1)
+        K = max(1, min(args.steps, 3))
+        h2d = rp_h.numel() * 4 + ci_h.numel() * 4 + va_h.numel() * 8 + b_h.numel() * 8
+        d2h = 2 * 8 * s.n
+
+        def e2e_step():
+            A.rowptr.copy_(rp_h, non_blocking=True)
+            A.colidx.copy_(ci_h, non_blocking=True)
+            A.val.copy_(va_h, non_blocking=True)
+            b.copy_(b_h, non_blocking=True)
+            g.gs_scale(A, b, p=2.0, ctx=ctx)
+            x1.zero_()
+            g.bicgstab_solve(A, b, x1, tol=TOL, ctx=ctx)
+            x2.zero_()
+            g.gmres_solve(A, b, x2, m=M_GMRES, tol=TOL, ctx=ctx)
+            xo1.copy_(x1, non_blocking=True)
+            xo2.copy_(x2, non_blocking=True)
+            torch.cuda.current_stream(dev).synchronize()
+
+        e2e_step()
+        barrier(dist, local)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(K):
+            e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        t_e = max_over_ranks(dist, f0.elapsed_time(f1) / 1e3)
+        e2e = {"value": sum_over_ranks(dist, SOLVES_PER_STEP * K) / t_e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": K}
+
+    roofline, kernels = None, None
+    if not args.no_profile and rank == 0:
+        roofline, kernels = profile_pass(g, ctx, A, val0, b, b0, s)
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        cpu = cpu_sample(s)
+
+    if rank == 0:
+        i1, i2 = infos[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+            "config": config_dict(s, world), "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "roofline": roofline, "cpu_baseline": cpu,
+            "solves": {"bicgstab": {k: i1[k] for k in ("iters", "conv_name", "relres_true", "ms")},
+                       "gmres30": {k: i2[k] for k in ("iters", "restarts", "conv_name", "relres_true", "ms")},
+                       "all_converged_below_tol": ok},
+            "kernels": kernels,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def profile_pass(g, ctx, A, val0, b, b0, s):
+    """Per-kernel device times from CUDA events around each launch (the same
+    kernels driven from a host loop), for the roofline of the dominant one."""
+    import torch
+
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    A.val.copy_(val0)
+    b.copy_(b0)
+    g.gs_scale(A, b, p=2.0, ctx=ctx)
+    agg = {}
+    for solver in ("bicgstab", "gmres"):
+        x = torch.zeros(s.n, dtype=torch.float64, device=A.val.device)
+        recs, info = g.profile_solve(A, b, x, solver=solver, m=M_GMRES, tol=TOL, max_iters=10000, ctx=ctx)
+        for name, step, ms in recs:
+            by, fl = kernel_cost(name, step, s.n, s.nnz)
+            a = agg.setdefault(name, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
+            a["launches"] += 1
+            a["ms"] += ms
+            a["bytes"] += by
+            a["flops"] += fl
+    total = sum(a["ms"] for a in agg.values())
+    kernels = {}
+    for name, a in sorted(agg.items(), key=lambda kv: -kv[1]["ms"]):
+        t = a["ms"] / 1e3
+        kernels[name] = {"launches": a["launches"], "ms_total": round(a["ms"], 3),
+                         "share": round(a["ms"] / total, 4),
+                         "GBps": round(a["bytes"] / t / 1e9, 1) if t > 0 else None,
+                         "fp64_TFLOPs": round(a["flops"] / t / 1e12, 4) if t > 0 else None}
+    dom, a = max(agg.items(), key=lambda kv: kv[1]["ms"])
+    t_avg = a["ms"] / a["launches"] / 1e3
+    gbs = a["bytes"] / a["launches"] / t_avg / 1e9
+    tfl = a["flops"] / a["launches"] / t_avg / 1e12
+    f_hbm, f_alu = gbs / hbm, tfl / FP64_PEAK_TFLOPS
+    if f_alu > f_hbm:
+        roof = {"bound": "alu", "achieved": round(tfl, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(f_alu, 4), "peak_source": "nominal GB300 FP64 rate (FMA probe measured 1.19)"}
+    else:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(f_hbm, 4),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    roof.update({"kernel": dom, "launches": a["launches"], "avg_us": round(t_avg * 1e6, 2),
+                 "share": kernels[dom]["share"], "hbm_frac": round(f_hbm, 4), "fp64_frac": round(f_alu, 4),
+                 "traffic": recorded_traffic(dom),
+                 "timing": "CUDA events around each launch, kernels driven from a host loop on the bench stream"})
+    return roof, kernels
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_sample(s, bcg_iters=20):
+    """The CPU oracle (one thread) on a bounded sample of the workload: GS(2),
+    bcg_iters Bi-CGSTAB iterations and one full GMRES(30) cycle, scaled to a
+    whole solve by the oracle's own iteration counts for this workload
+    (tests/golden/c2_oracle_counts.json)."""
+    import oracle
+
+    counts = json.load(open(os.path.join(ROOT, "tests", "golden", "c2_oracle_counts.json")))
+    t0 = time.perf_counter()
+    val, b, _ = oracle.gs_scale(s.rowptr, s.colidx, s.val, s.b, 2.0)
+    t_gs = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.bicgstab(s.rowptr, s.colidx, val, b, tol=TOL, maxit=bcg_iters)
+    t_b = (time.perf_counter() - t0) / bcg_iters
+    t0 = time.perf_counter()
+    oracle.gmres(s.rowptr, s.colidx, val, b, m=M_GMRES, tol=TOL, maxit=M_GMRES)
+    t_cyc = time.perf_counter() - t0
+    nb = counts["bicgstab"]["iters"]
+    ng = counts["gmres30"]["iters"]
+    t_step = t_gs + t_b * nb + t_cyc * math.ceil(ng / M_GMRES)
+    return {"value": SOLVES_PER_STEP / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"GS(2) + {bcg_iters} Bi-CGSTAB iterations + one GMRES(30) cycle on the 128^3 workload, "
+                      f"scaled to {nb} Bi-CGSTAB iterations and {ng} GMRES steps (the oracle's own counts)",
+            "sample_seconds": round(t_gs + t_b * bcg_iters + t_cyc, 2)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    s = workload(args.grid)
+    samples = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        c = cpu_sample(s, bcg_iters=10)
+        if i >= args.warmup:
+            samples.append((c, time.perf_counter() - t0))
+    val = statistics.mean(c["value"] for c, _ in samples)
+    c0 = samples[0][0]
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(t for _, t in samples), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+            "config": config_dict(s, world),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": c0["sample"]},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

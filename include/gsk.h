@@ -165,6 +165,30 @@ gsk_status gmres_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, i
 gsk_status bicgstab_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, double tol,
                           const gsk_opts* opts, gsk_info* info, void* stream);
 
+/* One timed kernel launch of gsk_profile_solve. */
+typedef struct {
+  int32_t kernel;  /* kernel id, named by gsk_kernel_name */
+  int32_t step;    /* Bi-CGSTAB: iteration; GMRES: Arnoldi index j (or -1) */
+  float ms;        /* device time between CUDA events around the launch */
+} gsk_launch_record;
+
+/* Name of a kernel id of gsk_launch_record ("" if unknown). */
+const char* gsk_kernel_name(int kernel);
+
+/*
+ * gsk_profile_solve -- runs the same kernels as gmres_solve (solver 0) or
+ * bicgstab_solve (solver 1) from a host loop on `stream` instead of one
+ * graph launch, with a CUDA event pair around every kernel launch, for at
+ * most max_iters iterations (Arnoldi steps for GMRES).  Up to `cap` records
+ * are written to recs (host) and their number to *nrec; `info` (host,
+ * optional) receives the outcome.  A profiling aid (the paper has no
+ * counterpart): the host reads the device state between launches, so the
+ * wall time is not that of a solve; the per-launch device times are.
+ */
+gsk_status gsk_profile_solve(gsk_ctx* ctx, int solver, const gsk_csr* A, const void* b, void* x, int m,
+                             double tol, const gsk_opts* opts, int max_iters, gsk_launch_record* recs, int cap,
+                             int* nrec, gsk_info* info, void* stream);
+
 /* Device workspace a solve of this shape needs (solver: 0 = GMRES, 1 =
  * Bi-CGSTAB), so that callers can budget HBM before admitting work. */
 gsk_status gsk_workspace_bytes(int n, int nnz, int solver, int m, int precision, size_t* bytes);

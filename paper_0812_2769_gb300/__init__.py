@@ -63,6 +63,10 @@ class InfoC(C.Structure):
         return d
 
 
+class LaunchRecordC(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("step", C.c_int32), ("ms", C.c_float)]
+
+
 _lib = None
 
 # every entry point of include/gsk.h, with its ctypes signature
@@ -79,6 +83,10 @@ SIGNATURES = {
     "bicgstab_solve": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_double,
                         C.POINTER(OptsC), C.POINTER(InfoC), C.c_void_p], C.c_int),
     "gsk_workspace_bytes": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+    "gsk_kernel_name": ([C.c_int], C.c_char_p),
+    "gsk_profile_solve": ([C.c_void_p, C.c_int, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                           C.POINTER(OptsC), C.c_int, C.POINTER(LaunchRecordC), C.c_int, C.POINTER(C.c_int),
+                           C.POINTER(InfoC), C.c_void_p], C.c_int),
 }
 
 
@@ -245,6 +253,25 @@ def bicgstab_solve(A: Csr, b, x, tol: float = 1e-8, options: OptsC | None = None
     ctx.check(lib().bicgstab_solve(ctx.handle, C.byref(Ac), _ptr(b), _ptr(x), float(tol), C.byref(o),
                                    C.byref(info) if sync else None, _stream_ptr(stream)))
     return info.as_dict() if sync else None
+
+
+def profile_solve(A: Csr, b, x, solver: str = "bicgstab", m: int = 30, tol: float = 1e-8,
+                  options: OptsC | None = None, max_iters: int = 50, ctx: Context | None = None, stream=None):
+    """Run a solver's kernels from a host loop with CUDA events around each
+    launch (a profiling aid).  Returns (records, info): records is a list of
+    (kernel name, step, ms) in launch order."""
+    ctx = ctx or default_context(A.val.device.index or 0)
+    Ac = A.c()
+    cap = 64 + 8 * max_iters + 16 * (max_iters // max(m, 1) + 2)
+    recs = (LaunchRecordC * cap)()
+    nrec = C.c_int()
+    info = InfoC()
+    o = options if options is not None else opts()
+    ctx.check(lib().gsk_profile_solve(ctx.handle, 0 if solver == "gmres" else 1, C.byref(Ac), _ptr(b), _ptr(x),
+                                      int(m), float(tol), C.byref(o), int(max_iters), recs, cap, C.byref(nrec),
+                                      C.byref(info), _stream_ptr(stream)))
+    out = [(lib().gsk_kernel_name(r.kernel).decode(), r.step, r.ms) for r in recs[: nrec.value]]
+    return out, info.as_dict()
 
 
 def workspace_bytes(n: int, nnz: int, solver: str = "bicgstab", m: int = 30, precision: int = PREC_F64) -> int:

@@ -129,6 +129,41 @@ gsk_status gsk_spmv(gsk_ctx* ctx, const gsk_csr* A, const void* x, void* y, void
   return gsk::launch_spmv(ctx, A, x, y, err, st);
 }
 
+const char* gsk_kernel_name(int k) {
+  static const char* names[gsk::kKCount] = {
+      "gs_norm(w)", "unit_check", "bcg_init", "bcg_k1_spmv_dot", "bcg_k2a_s_update", "bcg_k2b_spmv_dot",
+      "bcg_k3_xr_update", "bcg_k4_p_update", "bcg_kt_true_residual", "bcg_kr_finish", "gm_init_residual",
+      "gm_ga_spmv", "gm_gb_cgs_pass2", "gm_gc_cgs_pass3_givens", "gm_gy_backsolve", "gm_gx_x_update",
+      "gm_gr_restart_residual", "gm_gd_cgs_pass1"};
+  return (k >= 0 && k < gsk::kKCount) ? names[k] : "";
+}
+
+gsk_status gsk_profile_solve(gsk_ctx* ctx, int solver, const gsk_csr* A, const void* b, void* x, int m,
+                             double tol, const gsk_opts* opts_in, int max_iters, gsk_launch_record* recs, int cap,
+                             int* nrec, gsk_info* info, void* stream) {
+  if (!ctx) return GSK_ERR_ARG;
+  gsk_status s = gsk::check_csr(ctx, A);
+  if (s != GSK_OK) return s;
+  if (!recs || cap < 0 || max_iters < 0) return ctx->fail(GSK_ERR_ARG, "bad record buffer or max_iters");
+  gsk_opts opts;
+  if (opts_in) opts = *opts_in;
+  else gsk_opts_default(&opts);
+  if (opts.precision != GSK_PREC_F64) return ctx->fail(GSK_ERR_ARG, "profiling runs the FP64 solvers");
+  gsk::LaunchTimer T;
+  T.ctx = ctx;
+  T.st = (cudaStream_t)stream;
+  if (solver == 0) {
+    if (m < 1 || m > gsk::kMaxM) return ctx->fail(GSK_ERR_ARG, "m must be in 1..64");
+    s = gsk::gm_profile(ctx, A, b, x, m, tol, opts, max_iters, T, info);
+  } else if (solver == 1) {
+    s = gsk::bcg_profile(ctx, A, b, x, tol, opts, max_iters, T, info);
+  } else {
+    return ctx->fail(GSK_ERR_ARG, "solver must be 0 (GMRES) or 1 (Bi-CGSTAB)");
+  }
+  gsk_status s2 = T.finish(recs, cap, nrec);
+  return s != GSK_OK ? s : s2;
+}
+
 gsk_status gsk_workspace_bytes(int n, int nnz, int solver, int m, int precision, size_t* bytes) {
   if (!bytes || n < 0 || nnz < 0) return GSK_ERR_ARG;
   const size_t nn = (size_t)n;

@@ -67,55 +67,53 @@ __device__ __forceinline__ void warp_sum_table(const double* src, int stride, in
 }
 
 // Block-wide sum of nv per-thread values held in shared memory as
-// tab[k * BLOCK + t].  Result in res[k] (shared), valid after the call.
+// tab[k * BLOCK + t] (the table is consumed).  Result in res[k] (shared),
+// valid after the call.  Tree as in block_sum.
 template <int BLOCK>
 __device__ __forceinline__ void block_sum_table(double* tab, int nv, double* res) {
   __syncthreads();
-  constexpr int NW = BLOCK / 32;
-  const int w = warp_id();
-  // each warp takes whole rows k; a row of BLOCK entries is summed by the
-  // warp's lanes (BLOCK/32 each, sequential) and a fixed shuffle tree
-  for (int k = w; k < nv; k += NW) {
-    double s = 0.0;
 #pragma unroll
-    for (int q = 0; q < BLOCK / 32; ++q) s += tab[k * BLOCK + lane_id() * (BLOCK / 32) + q];
-    s = warp_allsum(s);
-    if (lane_id() == 0) res[k] = s;
+  for (int s = BLOCK / 2; s >= 32; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int k = 0; k < nv; ++k) tab[k * BLOCK + threadIdx.x] += tab[k * BLOCK + threadIdx.x + s];
+    __syncthreads();
+  }
+  // the remaining 32 partial sums of each value: one warp per value
+  for (int k = warp_id(); k < nv; k += BLOCK / 32) {
+    const double t = warp_allsum(tab[k * BLOCK + lane_id()]);
+    if (lane_id() == 0) res[k] = t;
   }
   __syncthreads();
 }
 
 // Block-wide sum of NV register values (all threads contribute).  Uses the
 // caller's shared scratch sm[NV * BLOCK]; totals in res[NV] (shared).
+// The values go through a shared-memory tree (BLOCK/2, BLOCK/4, ... 32
+// active threads) and one warp finishes with shuffles: about 12 warp-wide
+// FP64 additions per value instead of 45 for a shuffle tree in every warp,
+// which matters on a part with little FP64 throughput.
 template <int NV, int BLOCK>
 __device__ __forceinline__ void block_sum(const double (&v)[NV], double* sm, double* res) {
-  if (NV <= 4) {
-    // few values: warp trees, then one warp over the warp totals
-    constexpr int NW = BLOCK / 32;
-    __syncthreads();
-    double t[NV];
+  __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NV; ++k) t[k] = warp_allsum(v[k]);
-    if (lane_id() == 0) {
+  for (int k = 0; k < NV; ++k) sm[k * BLOCK + threadIdx.x] = v[k];
+  __syncthreads();
 #pragma unroll
-      for (int k = 0; k < NV; ++k) sm[k * NW + warp_id()] = t[k];
+  for (int s = BLOCK / 2; s >= 32; s >>= 1) {
+    if (threadIdx.x < s) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sm[k * BLOCK + threadIdx.x] += sm[k * BLOCK + threadIdx.x + s];
     }
     __syncthreads();
-    if (warp_id() == 0) {
-#pragma unroll
-      for (int k = 0; k < NV; ++k) {
-        double s = lane_id() < NW ? sm[k * NW + lane_id()] : 0.0;
-        s = warp_allsum(s);
-        if (lane_id() == 0) res[k] = s;
-      }
-    }
-    __syncthreads();
-  } else {
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV; ++k) sm[k * BLOCK + threadIdx.x] = v[k];
-    block_sum_table<BLOCK>(sm, NV, res);
   }
+  if (warp_id() == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const double t = warp_allsum(sm[k * BLOCK + lane_id()]);
+      if (lane_id() == 0) res[k] = t;
+    }
+  }
+  __syncthreads();
 }
 
 // Grid-wide deterministic sum of nv block totals blk[k] (shared memory, valid
@@ -232,17 +230,29 @@ __device__ __forceinline__ T csr_tile_row(const int* __restrict__ rowptr, const 
     }
     __syncwarp();
     if (ok && row < n) {
-      for (int k = rs - e0; k < re - e0; ++k) {
-        const int c = st.col[k];
-        if ((unsigned)c < (unsigned)n) sum = fma(st.val[k], (T)__ldg(x + c), sum);
+      const int base = rs - e0, len = re - rs;
+      int k = 0;
+      // pairs: two gathers of x in flight before the FMAs (column order kept)
+      for (; k + 1 < len; k += 2) {
+        const int c0 = st.col[base + k], c1 = st.col[base + k + 1];
+        const T a0 = st.val[base + k], a1 = st.val[base + k + 1];
+        T x0 = T(0), x1 = T(0);
+        if ((unsigned)c0 < (unsigned)n) x0 = (T)__ldg(x + c0); else atomicOr(err, kErrIndex);
+        if ((unsigned)c1 < (unsigned)n) x1 = (T)__ldg(x + c1); else atomicOr(err, kErrIndex);
+        sum = fma(a0, x0, sum);
+        sum = fma(a1, x1, sum);
+      }
+      if (k < len) {
+        const int c0 = st.col[base + k];
+        if ((unsigned)c0 < (unsigned)n) sum = fma(st.val[base + k], (T)__ldg(x + c0), sum);
         else atomicOr(err, kErrIndex);
       }
     }
     __syncwarp();
   } else if (ok && row < n) {
     for (int k = rs; k < re; ++k) {
-      const int c = __ldg(colidx + k);
-      if ((unsigned)c < (unsigned)n) sum = fma(__ldg(val + k), (T)__ldg(x + c), sum);
+      const int cc = __ldg(colidx + k);
+      if ((unsigned)cc < (unsigned)n) sum = fma(__ldg(val + k), (T)__ldg(x + cc), sum);
       else atomicOr(err, kErrIndex);
     }
   }

@@ -7,8 +7,9 @@
 // scale is folded into the next product instead of a separate normalisation
 // pass over V.
 //
-// One Arnoldi step j (k = j + 1 basis vectors) is three kernels:
-//   ga  w = A v_j -> V[:, j+1];  h1 = V_k^T w;  ||w||            (SpMV + multi-dot)
+// One Arnoldi step j (k = j + 1 basis vectors) is four kernels:
+//   ga  w = A v_j -> V[:, j+1];  ||w||                           (SpMV)
+//   gd  h1 = V_k^T w                                             (CGS pass 1, multi-dot)
 //   gb  w -= V_k h1;             h2 = V_k^T w                    (CGS pass 2)
 //   gc  w -= V_k h2;             ||w||  -> column j of H = h1 + h2,
 //       h_{j+1,j} = ||w||, earlier rotations applied, new rotation, g update,
@@ -35,7 +36,7 @@ namespace gsk {
 
 struct GmState {
   double rho0, mu0, tau, tol, est, mu_true, aw_norm;
-  int m, maxit, iters, restarts, conv, j, kcols, stop, est_hit, w_identity;
+  int m, maxit, iters, restarts, conv, j, kcols, stop, est_hit, w_identity, cont;
 };
 
 template <typename T>
@@ -55,7 +56,13 @@ struct GmArgs {
   unsigned* cnt;
   int* err;
   cudaGraphConditionalHandle h_outer, h_inner;
+  int in_graph;
 };
+
+template <typename T>
+__device__ __forceinline__ void gm_set_cond(const GmArgs<T>& a, cudaGraphConditionalHandle h, unsigned v) {
+  if (a.in_graph) cudaGraphSetConditional(h, v);
+}
 
 #define GM_TILE_LOOP(a) \
   for (int tile = blockIdx.x * kWarpsPerBlock + warp_id(), ntiles_ = ((a).n + 31) / 32; tile < ntiles_; \
@@ -159,24 +166,24 @@ __global__ void __launch_bounds__(kBlock) gm_residual(GmArgs<T> a) {
       S->kcols = 0;
     }
     S->stop = stop;
-    cudaGraphSetConditional(a.h_outer, (unsigned)!stop);
-    cudaGraphSetConditional(a.h_inner, (unsigned)!stop);
+    S->cont = !stop;
+    gm_set_cond(a, a.h_outer, (unsigned)!stop);
+    gm_set_cond(a, a.h_inner, (unsigned)!stop);
   }
 }
 
-// Arnoldi pass 1: w = A v_j stored in V[:, j+1]; h1 = V_k^T w; ||w||^2.
-template <typename T, int KP>
+// Arnoldi step, product: w = A v_j stored in V[:, j+1]; ||w||^2 (the
+// reference for the breakdown test).
+template <typename T>
 __global__ void __launch_bounds__(kBlock) gm_ga(GmArgs<T> a) {
   __shared__ GmSmem<T> sm;
-  __shared__ double res[KP + 1], tot[KP + 1];
+  __shared__ double res[1], tot[1];
   const GmState* S = a.S;
-  const int j = S->j, k = j + 1;
+  const int j = S->j;
   const T* vj = a.V + (long long)j * a.ldv;
-  T* wout = a.V + (long long)(j + 1) * a.ldv;
+  T* __restrict__ wout = a.V + (long long)(j + 1) * a.ldv;
   const double sj = a.sig[j];
-  double acc[KP], ww[1] = {0.0};
-#pragma unroll
-  for (int c = 0; c < KP; ++c) acc[c] = 0.0;
+  double ww[1] = {0.0};
   GM_TILE_LOOP(a) {
     const int i = tile * 32 + lane_id();
     const T av = csr_tile_row<T, T, kStageCap>(a.rowptr, a.colidx, a.val, vj, a.n, a.nnz, tile * 32,
@@ -184,18 +191,36 @@ __global__ void __launch_bounds__(kBlock) gm_ga(GmArgs<T> a) {
     if (i < a.n) {
       const T w = (T)(sj * (double)av);
       wout[i] = w;
-#pragma unroll
-      for (int c = 0; c < KP; ++c)
-        if (c < k) acc[c] = fma((double)a.V[(long long)c * a.ldv + i], (double)w, acc[c]);
       ww[0] = fma((double)w, (double)w, ww[0]);
     }
   }
-  // [h1_0 .. h1_{k-1}, ||w||^2] side by side for one grid reduction
-  block_sum_chunked<KP>(acc, k, sm.table, res);
-  block_sum_chunked<1>(ww, 1, sm.table, res + k);
-  if (grid_sum(res, k + 1, a.red, tot)) {
+  block_sum_chunked<1>(ww, 1, sm.table, res);
+  if (grid_sum(res, 1, a.red, tot) && threadIdx.x == 0) a.S->aw_norm = sqrt(tot[0]);
+}
+
+// CGS pass 1: h1 = sig .* (V_k^T w).
+template <typename T, int KP>
+__global__ void __launch_bounds__(kBlock) gm_gd(GmArgs<T> a) {
+  __shared__ double table[16 * kBlock], res[KP], tot[KP];
+  const GmState* S = a.S;
+  const int j = S->j, k = j + 1;
+  const T* __restrict__ wv = a.V + (long long)(j + 1) * a.ldv;
+  double acc[KP];
+#pragma unroll
+  for (int c = 0; c < KP; ++c) acc[c] = 0.0;
+  GM_ROW_LOOP(a) {
+    const double w = (double)wv[i];
+#pragma unroll
+    for (int c0 = 0; c0 < KP; c0 += 4)
+      if (c0 < k) {
+#pragma unroll
+        for (int c = c0; c < c0 + 4; ++c)
+          if (c < k) acc[c] = fma((double)a.V[(long long)c * a.ldv + i], w, acc[c]);
+      }
+  }
+  block_sum_chunked<KP>(acc, k, table, res);
+  if (grid_sum(res, k, a.red, tot)) {
     for (int c = threadIdx.x; c < k; c += kBlock) a.h1[c] = a.sig[c] * tot[c];
-    if (threadIdx.x == 0) a.S->aw_norm = sqrt(tot[k]);
   }
 }
 
@@ -214,13 +239,21 @@ __global__ void __launch_bounds__(kBlock) gm_gb(GmArgs<T> a) {
   GM_ROW_LOOP(a) {
     double w = (double)wv[i];
 #pragma unroll
-    for (int c = 0; c < KP; ++c)
-      if (c < k) w = fma(-(double)a.V[(long long)c * a.ldv + i], coef[c], w);
+    for (int c0 = 0; c0 < KP; c0 += 4)
+      if (c0 < k) {
+#pragma unroll
+        for (int c = c0; c < c0 + 4; ++c)
+          if (c < k) w = fma(-(double)a.V[(long long)c * a.ldv + i], coef[c], w);
+      }
     const T wt = (T)w;
     wv[i] = wt;
 #pragma unroll
-    for (int c = 0; c < KP; ++c)
-      if (c < k) acc[c] = fma((double)a.V[(long long)c * a.ldv + i], (double)wt, acc[c]);
+    for (int c0 = 0; c0 < KP; c0 += 4)
+      if (c0 < k) {
+#pragma unroll
+        for (int c = c0; c < c0 + 4; ++c)
+          if (c < k) acc[c] = fma((double)a.V[(long long)c * a.ldv + i], (double)wt, acc[c]);
+      }
   }
   block_sum_chunked<KP>(acc, k, table, res);
   if (grid_sum(res, k, a.red, tot)) {
@@ -242,8 +275,12 @@ __global__ void __launch_bounds__(kBlock) gm_gc(GmArgs<T> a) {
   GM_ROW_LOOP(a) {
     double w = (double)wv[i];
 #pragma unroll
-    for (int c = 0; c < KP; ++c)
-      if (c < k) w = fma(-(double)a.V[(long long)c * a.ldv + i], coef[c], w);
+    for (int c0 = 0; c0 < KP; c0 += 4)
+      if (c0 < k) {
+#pragma unroll
+        for (int c = c0; c < c0 + 4; ++c)
+          if (c < k) w = fma(-(double)a.V[(long long)c * a.ldv + i], coef[c], w);
+      }
     const T wt = (T)w;
     wv[i] = wt;
     acc[0] = fma((double)wt, (double)wt, acc[0]);
@@ -293,7 +330,8 @@ __global__ void __launch_bounds__(kBlock) gm_gc(GmArgs<T> a) {
       a.sig[j + 1] = 1.0 / hnext;
       S->j = j + 1;
     }
-    cudaGraphSetConditional(a.h_inner, (unsigned)cont);
+    S->cont = cont;
+    gm_set_cond(a, a.h_inner, (unsigned)cont);
   }
 }
 
@@ -319,17 +357,49 @@ __global__ void __launch_bounds__(kBlock) gm_gx(GmArgs<T> a) {
   GM_ROW_LOOP(a) {
     double x = (double)a.x[i];
 #pragma unroll
-    for (int c = 0; c < KP; ++c)
-      if (c < k) x = fma((double)a.V[(long long)c * a.ldv + i], coef[c], x);
+    for (int c0 = 0; c0 < KP; c0 += 4)
+      if (c0 < k) {
+#pragma unroll
+        for (int c = c0; c < c0 + 4; ++c)
+          if (c < k) x = fma((double)a.V[(long long)c * a.ldv + i], coef[c], x);
+      }
     a.x[i] = (T)x;
   }
 }
 
 // ------------------------------------------------------------------ host
 
+struct GmPlan {
+  int g_tile, g_vec, wmode, KP;
+  GmArgs<double> a;
+  double* wbuf;
+  GmState host_state;
+};
+
 template <int KP>
-static gsk_status gm_record(gsk_ctx* ctx, GmArgs<double>& a, int g_tile, int g_vec, int wmode, double* wbuf,
-                            int* wid_out, cudaGraphExec_t* exec_out) {
+static void gm_launch_kp(gsk_ctx* ctx, GmPlan& P, int k, cudaStream_t s) {
+  GmArgs<double>& a = P.a;
+  switch (k) {
+    case kKWeights: launch_gs_norm(ctx, a.n, a.nnz, a.rowptr, a.val, 2.0, P.wbuf, a.err, s); break;
+    case kKUnitCheck: launch_unit_check(ctx, a.n, P.wbuf, a.red, &a.S->w_identity, s); break;
+    case kKGmInit: gm_residual<double, true><<<P.g_tile, kBlock, 0, s>>>(a); break;
+    case kKGmGa: gm_ga<double><<<P.g_tile, kBlock, 0, s>>>(a); break;
+    case kKGmGd: gm_gd<double, KP><<<P.g_vec, kBlock, 0, s>>>(a); break;
+    case kKGmGb: gm_gb<double, KP><<<P.g_vec, kBlock, 0, s>>>(a); break;
+    case kKGmGc: gm_gc<double, KP><<<P.g_vec, kBlock, 0, s>>>(a); break;
+    case kKGmGy: gm_gy<double><<<1, 32, 0, s>>>(a); break;
+    case kKGmGx: gm_gx<double, KP><<<P.g_vec, kBlock, 0, s>>>(a); break;
+    case kKGmGr: gm_residual<double, false><<<P.g_tile, kBlock, 0, s>>>(a); break;
+  }
+}
+
+static void gm_launch(gsk_ctx* ctx, GmPlan& P, int k, cudaStream_t s) {
+  if (P.KP == 16) gm_launch_kp<16>(ctx, P, k, s);
+  else if (P.KP == 32) gm_launch_kp<32>(ctx, P, k, s);
+  else gm_launch_kp<64>(ctx, P, k, s);
+}
+
+static gsk_status gm_record(gsk_ctx* ctx, GmPlan& P, cudaGraphExec_t* exec_out) {
   cudaStream_t cs = ctx->capture;
   cudaGraph_t top = nullptr;
   GSK_CK(cudaGraphCreate(&top, 0));
@@ -337,6 +407,8 @@ static gsk_status gm_record(gsk_ctx* ctx, GmArgs<double>& a, int g_tile, int g_v
     cudaGraph_t g;
     ~Guard() { if (g) cudaGraphDestroy(g); }
   } guard{top};
+  GmArgs<double>& a = P.a;
+  a.in_graph = 1;
   GSK_CK(cudaGraphConditionalHandleCreate(&a.h_outer, top, 1u, cudaGraphCondAssignDefault));
   // top: [weights] -> init -> WHILE_outer{ WHILE_inner{ga, gb, gc} -> gy -> gx -> gr }
   // The init kernel sets the inner handle, which is created against the
@@ -348,34 +420,136 @@ static gsk_status gm_record(gsk_ctx* ctx, GmArgs<double>& a, int g_tile, int g_v
   GSK_CK(cudaGraphConditionalHandleCreate(&a.h_inner, obody, 1u, 0));
   Capture c0;
   GSK_CK(c0.begin(cs, top));
-  if (wmode == 0) {
-    launch_gs_norm(ctx, a.n, a.nnz, a.rowptr, a.val, 2.0, wbuf, a.err, cs);
-    launch_unit_check(ctx, a.n, wbuf, a.red, wid_out, cs);
+  if (P.wmode == 0) {
+    gm_launch(ctx, P, kKWeights, cs);
+    gm_launch(ctx, P, kKUnitCheck, cs);
   }
-  gm_residual<double, true><<<g_tile, kBlock, 0, cs>>>(a);
+  gm_launch(ctx, P, kKGmInit, cs);
   GSK_CK(c0.end());
   {
     std::vector<cudaGraphNode_t> to(c0.tail.size(), onode);
     GSK_CK(cudaGraphAddDependencies(top, c0.tail.data(), to.data(), nullptr, c0.tail.size()));
   }
-
   cudaGraphNode_t inode;
   cudaGraph_t ibody;
   GSK_CK(add_conditional(obody, {}, a.h_inner, cudaGraphCondTypeWhile, 1, &inode, &ibody));
   Capture c1;
   GSK_CK(c1.begin(cs, ibody));
-  gm_ga<double, KP><<<g_tile, kBlock, 0, cs>>>(a);
-  gm_gb<double, KP><<<g_vec, kBlock, 0, cs>>>(a);
-  gm_gc<double, KP><<<g_vec, kBlock, 0, cs>>>(a);
+  for (int k : {kKGmGa, kKGmGd, kKGmGb, kKGmGc}) gm_launch(ctx, P, k, cs);
   GSK_CK(c1.end());
   Capture c2;
   GSK_CK(c2.begin(cs, obody, {inode}));
-  gm_gy<double><<<1, 32, 0, cs>>>(a);
-  gm_gx<double, KP><<<g_vec, kBlock, 0, cs>>>(a);
-  gm_residual<double, false><<<g_tile, kBlock, 0, cs>>>(a);
+  for (int k : {kKGmGy, kKGmGx, kKGmGr}) gm_launch(ctx, P, k, cs);
   GSK_CK(c2.end());
   GSK_CK(cudaGraphInstantiate(exec_out, top, 0));
   return GSK_OK;
+}
+
+static gsk_status gm_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, int m, double tol,
+                             const gsk_opts& opts, GmPlan& P) {
+  if (A->dtype != GSK_F64) return ctx->fail(GSK_ERR_ARG, "the FP64 solver needs an FP64 matrix");
+  if (!(tol >= 0.0) || opts.maxit < 0) return ctx->fail(GSK_ERR_ARG, "bad tol/maxit");
+  if (A->n > 0 && (!b || !x)) return ctx->fail(GSK_ERR_ARG, "NULL b or x");
+  const int n = A->n;
+  P.wmode = opts.weights ? 2 : (opts.metric == GSK_METRIC_PLAIN ? 1 : 0);
+  P.KP = m <= 16 ? 16 : (m <= 32 ? 32 : 64);
+  // tile (SpMV) kernels carry no per-column accumulators: full occupancy
+  P.g_tile = ctx->grid_for((n + 31) / 32, kWarpsPerBlock, 8);
+  P.g_vec = ctx->grid_for(n, kBlock, P.KP <= 16 ? 4 : 2);
+  const int gmax = P.g_tile > P.g_vec ? P.g_tile : P.g_vec;
+  const long long ldv = ((long long)n + 63) / 64 * 64;
+  GmArgs<double>& a = P.a;
+  std::memset(&a, 0, sizeof(a));
+  auto layout = [&](Arena& ar) {
+    a.err = ar.take<int>(64);
+    a.cnt = ar.take<unsigned>(64);
+    a.red = take_red(ar, gmax, m + 2);
+    a.S = ar.take<GmState>(1);
+    a.H = ar.take<double>((size_t)(m + 1) * m);
+    a.g = ar.take<double>(m + 1);
+    a.cs = ar.take<double>(m);
+    a.sn = ar.take<double>(m);
+    a.y = ar.take<double>(m);
+    a.h1 = ar.take<double>(m + 1);
+    a.h2 = ar.take<double>(m + 1);
+    a.sig = ar.take<double>(m + 1);
+    a.V = ar.take<double>((size_t)ldv * (m + 1));
+    P.wbuf = P.wmode == 0 ? ar.take<double>(n) : nullptr;
+  };
+  Arena sizing;
+  layout(sizing);
+  gsk_status s = ctx->reserve(sizing.off);
+  if (s != GSK_OK) return s;
+  Arena ar{(char*)ctx->ws, ctx->ws_bytes, 0};
+  layout(ar);
+  a.n = n;
+  a.nnz = A->nnz;
+  a.m = m;
+  a.ldv = ldv;
+  a.rowptr = A->rowptr;
+  a.colidx = A->colidx;
+  a.val = (const double*)A->val;
+  a.b = (const double*)b;
+  a.x = (double*)x;
+  a.w = P.wmode == 0 ? P.wbuf : (P.wmode == 2 ? opts.weights : nullptr);
+  a.in_graph = 0;
+  GmState& hs = P.host_state;
+  std::memset(&hs, 0, sizeof(hs));
+  hs.tol = tol;
+  hs.m = m;
+  hs.maxit = opts.maxit;
+  hs.w_identity = P.wmode == 1 ? 1 : 0;
+  return GSK_OK;
+}
+
+static gsk_status gm_upload(gsk_ctx* ctx, GmPlan& P, cudaStream_t st) {
+  const char* end = (const char*)(P.a.red.counters + (P.a.red.maxgrid + kGroup - 1) / kGroup + 1);
+  GSK_CK(cudaMemsetAsync(ctx->ws, 0, end - (const char*)ctx->ws, st));
+  GSK_CK(cudaMemcpyAsync(P.a.S, &P.host_state, sizeof(GmState), cudaMemcpyHostToDevice, st));
+  return GSK_OK;
+}
+
+static gsk_status gm_readback(gsk_ctx* ctx, GmPlan& P, cudaStream_t st, GmState& out, int& bits) {
+  char* hp = (char*)ctx->host_pinned;
+  GSK_CK(cudaMemcpyAsync(hp, P.a.S, sizeof(GmState), cudaMemcpyDeviceToHost, st));
+  GSK_CK(cudaMemcpyAsync(hp + 512, P.a.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GSK_CK(cudaStreamSynchronize(st));
+  std::memcpy(&out, hp, sizeof(out));
+  std::memcpy(&bits, hp + 512, sizeof(int));
+  return GSK_OK;
+}
+
+gsk_status gm_profile(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, int m, double tol,
+                      const gsk_opts& opts, int max_iters, LaunchTimer& T, gsk_info* info) {
+  GmPlan P;
+  gsk_status s = gm_prepare(ctx, A, b, x, m, tol, opts, P);
+  if (s != GSK_OK) return s;
+  if (A->n == 0) return GSK_OK;
+  if ((s = gm_upload(ctx, P, T.st)) != GSK_OK) return s;
+  auto timed = [&](int k, int step) -> gsk_status {
+    return T.time(k, step, [&](cudaStream_t st) { gm_launch(ctx, P, k, st); });
+  };
+  if (P.wmode == 0) {
+    if ((s = timed(kKWeights, -1)) != GSK_OK) return s;
+    if ((s = timed(kKUnitCheck, -1)) != GSK_OK) return s;
+  }
+  if ((s = timed(kKGmInit, -1)) != GSK_OK) return s;
+  GmState st;
+  int bits = 0;
+  if ((s = gm_readback(ctx, P, T.st, st, bits)) != GSK_OK) return s;
+  while (!st.stop && !bits && st.iters < max_iters) {
+    do {
+      const int j = st.j;
+      for (int k : {kKGmGa, kKGmGd, kKGmGb, kKGmGc})
+        if ((s = timed(k, j)) != GSK_OK) return s;
+      if ((s = gm_readback(ctx, P, T.st, st, bits)) != GSK_OK) return s;
+    } while (st.cont && !bits && st.iters < max_iters);
+    for (int k : {kKGmGy, kKGmGx, kKGmGr})
+      if ((s = timed(k, -1)) != GSK_OK) return s;
+    if ((s = gm_readback(ctx, P, T.st, st, bits)) != GSK_OK) return s;
+  }
+  if (info) *info = gsk_info{st.iters, st.restarts, 0, 0, st.conv, st.mu_true, st.est, 0.f};
+  return err_bits_status(ctx, bits);
 }
 
 }  // namespace gsk
@@ -392,95 +566,30 @@ extern "C" gsk_status gmres_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b,
   else gsk_opts_default(&opts);
   if (m < 1 || m > kMaxM) return ctx->fail(GSK_ERR_ARG, "m must be in 1..64");
   if (opts.precision == GSK_PREC_MIXED) return gmres_solve_mixed(ctx, A, b, x, m, tol, &opts, info, stream);
-  if (A->dtype != GSK_F64) return ctx->fail(GSK_ERR_ARG, "the FP64 solver needs an FP64 matrix");
-  if (!(tol >= 0.0) || opts.maxit < 0) return ctx->fail(GSK_ERR_ARG, "bad tol/maxit");
-  if (A->n > 0 && (!b || !x)) return ctx->fail(GSK_ERR_ARG, "NULL b or x");
   cudaStream_t st = (cudaStream_t)stream;
-  const int n = A->n;
-  if (n == 0) {
+  GmPlan P;
+  if ((s = gm_prepare(ctx, A, b, x, m, tol, opts, P)) != GSK_OK) return s;
+  if (A->n == 0) {
     if (info) *info = gsk_info{0, 0, 0, 0, GSK_CONVERGED, 0.0, 0.0, 0.f};
     return GSK_OK;
   }
-  const int wmode = opts.weights ? 2 : (opts.metric == GSK_METRIC_PLAIN ? 1 : 0);
-  const int KP = m <= 16 ? 16 : (m <= 32 ? 32 : 64);
-  const int g_tile = ctx->grid_for((n + 31) / 32, kWarpsPerBlock, KP <= 16 ? 4 : 2);
-  const int g_vec = ctx->grid_for(n, kBlock, KP <= 16 ? 4 : 2);
-  const int gmax = g_tile > g_vec ? g_tile : g_vec;
-  const long long ldv = ((long long)n + 63) / 64 * 64;
-
-  GmArgs<double> a;
-  std::memset(&a, 0, sizeof(a));
-  double* wbuf = nullptr;
-  int* wid_out = nullptr;
-  auto layout = [&](Arena& ar) {
-    a.err = ar.take<int>(64);
-    a.S = ar.take<GmState>(1);
-    a.cnt = ar.take<unsigned>(64);
-    a.red = take_red(ar, gmax, m + 2);
-    a.H = ar.take<double>((size_t)(m + 1) * m);
-    a.g = ar.take<double>(m + 1);
-    a.cs = ar.take<double>(m);
-    a.sn = ar.take<double>(m);
-    a.y = ar.take<double>(m);
-    a.h1 = ar.take<double>(m + 1);
-    a.h2 = ar.take<double>(m + 1);
-    a.sig = ar.take<double>(m + 1);
-    a.V = ar.take<double>((size_t)ldv * (m + 1));
-    wbuf = wmode == 0 ? ar.take<double>(n) : nullptr;
-  };
-  Arena sizing;
-  layout(sizing);
-  if ((s = ctx->reserve(sizing.off)) != GSK_OK) return s;
-  Arena ar{(char*)ctx->ws, ctx->ws_bytes, 0};
-  layout(ar);
-  a.n = n;
-  a.nnz = A->nnz;
-  a.m = m;
-  a.ldv = ldv;
-  a.rowptr = A->rowptr;
-  a.colidx = A->colidx;
-  a.val = (const double*)A->val;
-  a.b = (const double*)b;
-  a.x = (double*)x;
-  a.w = wmode == 0 ? wbuf : (wmode == 2 ? opts.weights : nullptr);
-  wid_out = &a.S->w_identity;
-
-  std::vector<uint64_t> key = {0, (uint64_t)n, (uint64_t)A->nnz, (uint64_t)m, (uint64_t)A->rowptr,
-                               (uint64_t)A->colidx, (uint64_t)A->val, (uint64_t)b, (uint64_t)x, (uint64_t)wmode,
-                               (uint64_t)a.w, (uint64_t)ctx->ws};
+  std::vector<uint64_t> key = {0, (uint64_t)A->n, (uint64_t)A->nnz, (uint64_t)m, (uint64_t)A->rowptr,
+                               (uint64_t)A->colidx, (uint64_t)A->val, (uint64_t)b, (uint64_t)x, (uint64_t)P.wmode,
+                               (uint64_t)P.a.w, (uint64_t)ctx->ws};
   GraphEntry* ge = ctx->find_graph(key);
   if (!ge) {
     cudaGraphExec_t ex = nullptr;
-    if (KP == 16) s = gm_record<16>(ctx, a, g_tile, g_vec, wmode, wbuf, wid_out, &ex);
-    else if (KP == 32) s = gm_record<32>(ctx, a, g_tile, g_vec, wmode, wbuf, wid_out, &ex);
-    else s = gm_record<64>(ctx, a, g_tile, g_vec, wmode, wbuf, wid_out, &ex);
-    if (s != GSK_OK) return s;
+    if ((s = gm_record(ctx, P, &ex)) != GSK_OK) return s;
     ge = ctx->add_graph(key, ex);
   }
-
-  GmState hs;
-  std::memset(&hs, 0, sizeof(hs));
-  hs.tol = tol;
-  hs.m = m;
-  hs.maxit = opts.maxit;
-  hs.w_identity = wmode == 1 ? 1 : 0;
   GSK_CK(cudaEventRecord(ctx->ev0, st));
-  // error word, counters and reduction scratch sit at the start of the
-  // workspace; other solves lay the workspace out differently, so clear them
-  GSK_CK(cudaMemsetAsync(ctx->ws, 0, (char*)(a.red.counters + (a.red.maxgrid + kGroup - 1) / kGroup + 1) -
-                                         (char*)ctx->ws, st));
-  GSK_CK(cudaMemcpyAsync(a.S, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+  if ((s = gm_upload(ctx, P, st)) != GSK_OK) return s;
   GSK_CK(cudaGraphLaunch(ge->exec, st));
   GSK_CK(cudaEventRecord(ctx->ev1, st));
   if (!info) return GSK_OK;
-  char* hp = (char*)ctx->host_pinned;
-  GSK_CK(cudaMemcpyAsync(hp, a.S, sizeof(GmState), cudaMemcpyDeviceToHost, st));
-  GSK_CK(cudaMemcpyAsync(hp + 512, a.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  GSK_CK(cudaStreamSynchronize(st));
   GmState out;
-  std::memcpy(&out, hp, sizeof(out));
-  int bits;
-  std::memcpy(&bits, hp + 512, sizeof(int));
+  int bits = 0;
+  if ((s = gm_readback(ctx, P, st, out, bits)) != GSK_OK) return s;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
   *info = gsk_info{out.iters, out.restarts, 0, 0, out.conv, out.mu_true, out.est, ms};

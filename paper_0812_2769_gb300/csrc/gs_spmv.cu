@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kBlock) spmv_kernel(int n, int nnz, const int*
 // none: the stopping-test weights are then the identity and are not loaded.
 __global__ void __launch_bounds__(kBlock) unit_check_kernel(int n, const double* __restrict__ w, GridRed red,
                                                             int* out) {
-  __shared__ double sm[4 * kWarpsPerBlock], blk[1], tot[1];
+  __shared__ double sm[kBlock], blk[1], tot[1];
   const long long lo = __double_as_longlong(1.0 - 4.0 * 2.220446049250313e-16);
   const long long hi = __double_as_longlong(1.0 + 4.0 * 2.220446049250313e-16);
   int cnt = 0;

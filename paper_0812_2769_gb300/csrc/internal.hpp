@@ -116,6 +116,59 @@ inline gsk_status err_bits_status(gsk_ctx* ctx, int bits) {
   return GSK_OK;
 }
 
+// Kernel identifiers used by the stream-mode profiler (gsk_profile_solve).
+enum KernelId : int {
+  kKWeights = 0, kKUnitCheck, kKBcgInit, kKBcgK1, kKBcgK2a, kKBcgK2b, kKBcgK3, kKBcgK4, kKBcgKt, kKBcgKr,
+  kKGmInit, kKGmGa, kKGmGb, kKGmGc, kKGmGy, kKGmGx, kKGmGr, kKGmGd, kKCount
+};
+
+// Times kernel launches in stream mode with a CUDA event pair around each.
+struct LaunchTimer {
+  gsk_ctx* ctx = nullptr;
+  cudaStream_t st = nullptr;
+  std::vector<cudaEvent_t> evs;
+  std::vector<std::pair<int, int>> ids;
+
+  template <class F>
+  gsk_status time(int kernel, int step, F&& launch) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) {
+      launch(st);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e0) evs.push_back(e0);
+    if (e1) evs.push_back(e1);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "timed launch");
+    ids.push_back({kernel, step});
+    return GSK_OK;
+  }
+  // After the stream is synchronised: writes up to cap records.
+  gsk_status finish(gsk_launch_record* recs, int cap, int* nrec) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaStreamSynchronize");
+    int n = 0;
+    for (size_t i = 0; i < ids.size() && n < cap; ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, evs[2 * i], evs[2 * i + 1]);
+      recs[n++] = gsk_launch_record{ids[i].first, ids[i].second, ms};
+    }
+    if (nrec) *nrec = n;
+    return GSK_OK;
+  }
+  ~LaunchTimer() {
+    for (auto ev : evs) cudaEventDestroy(ev);
+  }
+};
+
+gsk_status bcg_profile(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, double tol, const gsk_opts& opts,
+                       int max_iters, LaunchTimer& T, gsk_info* info);
+gsk_status gm_profile(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, int m, double tol,
+                      const gsk_opts& opts, int max_iters, LaunchTimer& T, gsk_info* info);
+
 // launchers implemented in the .cu files (capture-safe: no synchronisation)
 gsk_status launch_spmv(gsk_ctx* ctx, const gsk_csr* A, const void* x, void* y, int* err, cudaStream_t st);
 void launch_gs_norm(gsk_ctx* ctx, int n, int nnz, const int* rowptr, const double* val, double p, double* d,

@@ -57,13 +57,17 @@ def test_gs_scale_extreme_magnitudes():
 
 
 def _expect_error(sys_, status, p=2.0):
+    import torch
+
     g = gsk()
     A, b = to_dev(g, sys_)
     before = A.val.clone(), b.clone()
     with pytest.raises(g.GskError) as ei:
         g.gs_scale(A, b, p=p)
     assert ei.value.status == status
-    assert A.val.equal(before[0]) and b.equal(before[1])  # nothing modified
+    # nothing modified (bitwise, so NaN entries compare equal to themselves)
+    assert A.val.view(torch.int64).equal(before[0].view(torch.int64))
+    assert b.view(torch.int64).equal(before[1].view(torch.int64))
 
 
 def test_gs_zero_row_is_an_error_and_leaves_input():
