@@ -135,6 +135,31 @@ void gsk_opts_default(gsk_opts* opts);
 gsk_status gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, void* stream);
 
 /*
+ * gs_scale_static -- the same GS(p) scaling as gs_scale for callers that may
+ * not allocate device memory: code running where the memory is owned by
+ * someone else (a host application with a fixed device-memory budget or its
+ * own pool, a plugin that must not touch the allocator) and so cannot create
+ * a gsk_ctx, whose workspace is allocated.  The paper has no counterpart; it
+ * is an interface variant of gs_scale.
+ * It takes no context and calls no allocating CUDA routine.  Its scratch (an
+ * error word and, when d_out is NULL, the per-row scales) is a fixed array of
+ * 8 MiB + 256 B compiled into the library, which every GPU that loads the
+ * library holds until the process exits.
+ *   A, b, p, d_out, stream   as for gs_scale (device pointers, caller-owned)
+ * Limits and errors: with d_out == NULL, at most 1,048,576 rows (larger n
+ * returns GSK_ERR_ARG; pass d_out to scale larger systems, then only the
+ * error word is used); also GSK_ERR_ARG / GSK_ERR_ZERO_ROW / GSK_ERR_NONFINITE
+ * as gs_scale (A and b are left unmodified on error), GSK_ERR_CUDA if a CUDA
+ * call fails.  No error text is kept (there is no context).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array and clears the
+ * error word itself; calls whose work overlaps on the GPU (other streams, other
+ * threads) race on the array, so serialise them.  Synchronises `stream`.
+ */
+gsk_status gs_scale_static(gsk_csr* A, void* b, double p, double* d_out, void* stream);
+
+/*
  * gsk_spmv -- y = A x, the product every Krylov step performs (Sec. 2).
  *   x, y   device [n] of A's dtype; x and y must not overlap.
  * Asynchronous on `stream`.

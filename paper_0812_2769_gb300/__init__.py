@@ -77,6 +77,7 @@ SIGNATURES = {
     "gsk_last_error": ([C.c_void_p], C.c_char_p),
     "gsk_opts_default": ([C.POINTER(OptsC)], None),
     "gs_scale": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p], C.c_int),
+    "gs_scale_static": ([C.POINTER(CsrC), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p], C.c_int),
     "gsk_spmv": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gmres_solve": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                      C.POINTER(OptsC), C.POINTER(InfoC), C.c_void_p], C.c_int),
@@ -220,6 +221,18 @@ def gs_scale(A: Csr, b=None, p: float = 2.0, d_out=None, ctx: Context | None = N
     ctx = ctx or default_context(A.val.device.index or 0)
     Ac = A.c()
     ctx.check(lib().gs_scale(ctx.handle, C.byref(Ac), _ptr(b), float(p), _ptr(d_out), _stream_ptr(stream)))
+    return d_out
+
+
+def gs_scale_static(A: Csr, b=None, p: float = 2.0, d_out=None, stream=None):
+    """GS(p) in place without any device allocation (no context): for callers
+    that may not allocate device memory.  Scratch is a fixed array inside the
+    library (at most 1,048,576 rows when d_out is None); calls that overlap on
+    the GPU race on it.  Raises GskError with the status on failure."""
+    Ac = A.c()
+    st = lib().gs_scale_static(C.byref(Ac), _ptr(b), float(p), _ptr(d_out), _stream_ptr(stream))
+    if st != OK:
+        raise GskError(st, "gs_scale_static failed")
     return d_out
 
 

@@ -7,6 +7,8 @@
 // multiplies row i of A and b_i by d_i only if no error was recorded.  Both
 // stage each 32-row tile's nonzeros through shared memory so that global
 // loads and stores are coalesced and each lane works on its own row.
+#include <mutex>
+
 #include "internal.hpp"
 
 namespace gsk {
@@ -238,3 +240,91 @@ gsk_status run_gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_o
 }
 
 }  // namespace gsk
+
+// --------------------------------------------------- allocation-free GS(p)
+//
+// gs_scale_static: the same two GS(p) kernels as gs_scale, for callers that
+// must not allocate device memory (and so cannot create a gsk_ctx, whose
+// workspace is allocated).  Its scratch -- the error word and, when the caller
+// passes no d_out, the per-row scales -- lives in the file-scope array below,
+// which every device that loads the library holds until the process exits.
+namespace gsk {
+namespace {
+constexpr int kStaticMaxRows = 1 << 20;  // rows whose scales fit in the array
+constexpr size_t kStaticHeader = 256;    // error word (padded)
+constexpr size_t kStaticBytes = kStaticHeader + sizeof(double) * (size_t)kStaticMaxRows;  // 8 MiB + 256 B
+constexpr int kStaticMaxDevices = 64;
+
+struct StaticDevice {
+  void* scratch;  // device address of g_gs_static_scratch on this device
+  int sms;
+  bool ready;
+};
+StaticDevice g_static_dev[kStaticMaxDevices];
+std::mutex g_static_mu;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_gs_static_scratch[kStaticBytes];
+
+// Once per device, with that device current: look up the array's device
+// address (host code cannot use the symbol itself) and the SM count.
+static gsk_status static_setup(int dev, StaticDevice** out) {
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  StaticDevice& d = g_static_dev[dev];
+  if (!d.ready) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_gs_static_scratch) != cudaSuccess || p == nullptr) return GSK_ERR_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      return GSK_ERR_CUDA;
+    d.scratch = p;
+    d.sms = sms;
+    d.ready = true;
+  }
+  *out = &d;
+  return GSK_OK;
+}
+
+}  // namespace gsk
+
+extern "C" gsk_status gs_scale_static(gsk_csr* A, void* b, double p, double* d_out, void* stream) {
+  using namespace gsk;
+  if (!A || A->n < 0 || A->nnz < 0) return GSK_ERR_ARG;
+  if (A->n > 0 && (!A->rowptr || (A->nnz > 0 && !A->val))) return GSK_ERR_ARG;
+  if (A->dtype != GSK_F64 && A->dtype != GSK_F32) return GSK_ERR_ARG;
+  if (!(p >= 1.0)) return GSK_ERR_ARG;
+  if (!d_out && A->n > kStaticMaxRows) return GSK_ERR_ARG;  // the scales would not fit
+  if (A->n == 0) return GSK_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GSK_ERR_CUDA;
+  if (dev < 0 || dev >= kStaticMaxDevices) return GSK_ERR_ARG;
+  StaticDevice* sd = nullptr;
+  gsk_status s = static_setup(dev, &sd);
+  if (s != GSK_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* err = (int*)sd->scratch;
+  double* d = d_out ? d_out : (double*)((char*)sd->scratch + kStaticHeader);
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return GSK_ERR_CUDA;  // left set by the last call
+  const int pmode = p == 1.0 ? kP1 : (p == 2.0 ? kP2 : (p > 1e300 ? kPInf : kPGen));
+  long long g = ((long long)(A->n + 31) / 32 + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int grid = (int)(g < (long long)sd->sms * 8 ? (g < 1 ? 1 : g) : (long long)sd->sms * 8);
+  const int n = A->n;
+  if (A->dtype == GSK_F64) {
+    gs_norm_kernel<double><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const double*)A->val,
+                                                     (const double*)b, pmode, p, d, err);
+    gs_apply_kernel<double><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (double*)A->val, (double*)b, d, err);
+  } else {
+    gs_norm_kernel<float><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const float*)A->val,
+                                                    (const float*)b, pmode, p, d, err);
+    gs_apply_kernel<float><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (float*)A->val, (float*)b, d, err);
+  }
+  if (cudaGetLastError() != cudaSuccess) return GSK_ERR_CUDA;
+  int bits = 0;
+  if (cudaMemcpyAsync(&bits, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return GSK_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return GSK_ERR_CUDA;
+  if (bits & kErrIndex) return GSK_ERR_ARG;
+  if (bits & kErrNonFinite) return GSK_ERR_NONFINITE;
+  if (bits & kErrZeroRow) return GSK_ERR_ZERO_ROW;
+  return GSK_OK;
+}
+
