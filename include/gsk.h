@@ -86,9 +86,13 @@ typedef struct {
                              metric); NULL = derive them from `metric` */
   double inner_tol;       /* mixed precision: relative tolerance of each FP32
                              inner solve, default 1e-5 */
-  int32_t inner_maxit;    /* mixed precision: steps per inner solve, default 3*m
-                             (GMRES) or 300 (Bi-CGSTAB) */
-  int32_t max_refinements;/* mixed precision: outer FP64 steps, default 50 */
+  int32_t inner_maxit;    /* mixed precision: iterations per inner solve; 0 (the
+                             default) means m for GMRES (one cycle) and maxit
+                             for Bi-CGSTAB */
+  int32_t max_refinements;/* mixed precision: cap on outer FP64 refinement steps
+                             (for GMRES one step is one inner cycle); 0, the
+                             default, means no cap beyond maxit, which always
+                             bounds the total inner iterations */
 } gsk_opts;
 
 /* Result of a solve (host memory). */

@@ -207,7 +207,7 @@ def _ptr(t):
 
 
 def opts(maxit=10000, refresh=3, precision=PREC_F64, metric=METRIC_GS2, weights=None, inner_tol=1e-5,
-         inner_maxit=0, max_refinements=50) -> OptsC:
+         inner_maxit=0, max_refinements=0) -> OptsC:
     o = OptsC()
     lib().gsk_opts_default(C.byref(o))
     o.maxit, o.refresh, o.precision, o.metric = maxit, refresh, precision, metric

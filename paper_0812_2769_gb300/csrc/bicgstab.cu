@@ -1,399 +1,9 @@
-// Bi-CGSTAB (Sec. 2; van der Vorst 1992) with every scalar and every
-// stopping decision on the device.
-//
-// One iteration is the kernel chain
-//   k1  v = A p,           sigma = <rh, v>, ||v||         -> alpha or breakdown
-//   k2a s = r - alpha v,   ||W s||                         -> half-step exit?
-//   k2b t = A s,           <t, s>, <t, t>                  -> omega or breakdown
-//   k3  x += alpha p + omega s, r = s - omega t,
-//                          <rh, r>, ||W r||, ||r||         -> beta, flags
-//   then either k4  p = r + beta (p - omega v)             (keep iterating)
-//   or          kt  t = b - A x, ||W t||, ||t||            (true residual)
-//               kr  finish, or refresh r = rh = p = t
-// The chain is recorded once into a CUDA graph: a WHILE node repeats the
-// iteration and an IF/ELSE node picks k4 or kt+kr, both driven by values the
-// kernels set on the device, so a solve is one graph launch.  The same
-// kernels can also be driven from a host loop with a CUDA event around each
-// launch (gsk_profile_solve); every kernel then checks the device flags
-// itself, which the graph's conditional nodes make redundant.
-//
-// The breakdown tolerance is 1e-16 * DBL_EPSILON relative to the vector
-// norms (Sec. 2.2).  The stopping metric is ||W(b - Ax)|| / ||W(b - Ax0)||
-// with W the GS(2) scales of A (Sec. 2.2); when W is the identity to within
-// 4 ulp (an already GS(2)-scaled system) the weight loads are skipped and
-// ||r|| is taken from ||W r||.
-#include <cfloat>
-
+// Bi-CGSTAB host driver: graph recording, workspace layout, the C ABI entry
+// point and the stream-mode profiler.  The kernels are in bicgstab_kernels.cuh.
+#include "bicgstab_kernels.cuh"
 #include "graph.hpp"
-#include "internal.hpp"
 
 namespace gsk {
-
-struct BcgState {
-  double rho, alpha, omega, beta, rhn, mu0, mu_s, mu_rec, mu_true, tt_true, tol, brk;
-  int maxit, refresh_left, iters, refreshes, conv, stop, halfexit, check, active, w_identity;
-};
-
-template <typename T>
-struct BcgArgs {
-  int n, nnz;
-  const int* rowptr;
-  const int* colidx;
-  const T* val;
-  const T* b;
-  T* x;
-  T *r, *rh, *p, *v, *s, *t;
-  const double* w;
-  BcgState* S;
-  GridRed red;
-  unsigned* cnt;
-  int* err;
-  cudaGraphConditionalHandle h_while, h_if;
-  int in_graph;
-};
-
-template <typename T>
-__device__ __forceinline__ void set_cond(const BcgArgs<T>& a, cudaGraphConditionalHandle h, unsigned v) {
-  if (a.in_graph) cudaGraphSetConditional(h, v);
-}
-
-#define BCG_TILE_LOOP(a) \
-  for (int tile = blockIdx.x * kWarpsPerBlock + warp_id(), ntiles_ = ((a).n + 31) / 32; tile < ntiles_; \
-       tile += gridDim.x * kWarpsPerBlock)
-
-// Two rows per thread per trip (i and i + stride) so that each thread keeps
-// twice the loads in flight; the row-to-thread map depends only on the grid.
-#define BCG_ROW2_LOOP(a)                                                        \
-  for (int i = blockIdx.x * kBlock + threadIdx.x, stride_ = gridDim.x * kBlock; \
-       i < (a).n; i += 2 * stride_)
-
-__device__ __forceinline__ double wgt(const double* w, bool wid, int i) { return wid ? 1.0 : __ldg(w + i); }
-
-template <typename T>
-__global__ void __launch_bounds__(kBlock) bcg_init(BcgArgs<T> a) {
-  __shared__ TileStage<T, kStageCap> stage[kWarpsPerBlock];
-  __shared__ double blk[2], tot[2];
-  double* sm = reinterpret_cast<double*>(stage);  // reduction scratch after the tile loop
-  BcgState* S = a.S;
-  const bool wid = S->w_identity;
-  double acc[2] = {0.0, 0.0};
-  BCG_TILE_LOOP(a) {
-    const int i = tile * 32 + lane_id();
-    const T ax = csr_tile_row<T, T, kStageCap>(a.rowptr, a.colidx, a.val, a.x, a.n, a.nnz, tile * 32,
-                                                 stage[warp_id()], a.err);
-    if (i < a.n) {
-      const T r = a.b[i] - ax;
-      a.r[i] = r;
-      a.rh[i] = r;
-      a.p[i] = r;
-      const double wr = wgt(a.w, wid, i) * (double)r;
-      acc[0] = fma(wr, wr, acc[0]);
-      acc[1] = fma((double)r, (double)r, acc[1]);
-    }
-  }
-  block_sum<2, kBlock>(acc, sm, blk);
-  if (grid_sum(blk, 2, a.red, tot) && threadIdx.x == 0) {
-    const int e = *(volatile int*)a.err;
-    const double mu0 = sqrt(tot[0]);
-    S->iters = 0;
-    S->refreshes = 0;
-    S->halfexit = 0;
-    S->check = 0;
-    S->mu0 = mu0;
-    S->rho = tot[1];
-    S->rhn = sqrt(tot[1]);
-    S->mu_rec = 1.0;
-    S->mu_true = 1.0;
-    S->conv = GSK_MAXIT;
-    int active = 1;
-    if (e) {
-      active = 0;
-    } else if (!isfinite(mu0)) {
-      atomicOr(a.err, kErrNonFinite);
-      active = 0;
-    } else if (mu0 == 0.0) {
-      S->conv = GSK_CONVERGED;
-      S->mu_true = 0.0;
-      S->mu_rec = 0.0;
-      active = 0;
-    } else if (S->maxit <= 0) {
-      active = 0;
-    }
-    S->stop = !active;
-    S->active = active;
-    set_cond(a, a.h_while, active);
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kBlock) bcg_k1(BcgArgs<T> a) {
-  BcgState* S = a.S;
-  if (S->stop) return;
-  __shared__ TileStage<T, kStageCap> stage[kWarpsPerBlock];
-  __shared__ double blk[2], tot[2];
-  double* sm = reinterpret_cast<double*>(stage);  // reduction scratch after the tile loop
-  const T* __restrict__ rh = a.rh;
-  T* __restrict__ vout = a.v;
-  double acc[2] = {0.0, 0.0};
-  BCG_TILE_LOOP(a) {
-    const int i = tile * 32 + lane_id();
-    const T v = csr_tile_row<T, T, kStageCap>(a.rowptr, a.colidx, a.val, a.p, a.n, a.nnz, tile * 32,
-                                                stage[warp_id()], a.err);
-    if (i < a.n) {
-      vout[i] = v;
-      acc[0] = fma((double)rh[i], (double)v, acc[0]);
-      acc[1] = fma((double)v, (double)v, acc[1]);
-    }
-  }
-  block_sum<2, kBlock>(acc, sm, blk);
-  if (grid_sum(blk, 2, a.red, tot) && threadIdx.x == 0) {
-    const double sigma = tot[0], vn = sqrt(tot[1]);
-    if (*(volatile int*)a.err) {
-      S->stop = 1;
-    } else if (!(fabs(sigma) > S->brk * S->rhn * vn)) {
-      S->conv = GSK_BREAKDOWN;
-      S->stop = 1;
-    } else {
-      S->alpha = S->rho / sigma;
-    }
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kBlock) bcg_k2a(BcgArgs<T> a) {
-  BcgState* S = a.S;
-  if (S->stop) return;
-  __shared__ double sm[1 * kBlock], blk[1], tot[1];
-  const double alpha = S->alpha;
-  const bool wid = S->w_identity;
-  const T* __restrict__ r = a.r;
-  const T* __restrict__ v = a.v;
-  T* __restrict__ s = a.s;
-  double acc[1] = {0.0};
-  BCG_ROW2_LOOP(a) {
-    const int i2 = i + stride_;
-    const bool two = i2 < a.n;
-    const double r1 = (double)r[i], v1 = (double)v[i];
-    const double r2 = two ? (double)r[i2] : 0.0, v2 = two ? (double)v[i2] : 0.0;
-    const T s1 = (T)fma(-alpha, v1, r1);
-    s[i] = s1;
-    double w1 = (double)s1;
-    if (!wid) w1 *= __ldg(a.w + i);
-    acc[0] = fma(w1, w1, acc[0]);
-    if (two) {
-      const T s2 = (T)fma(-alpha, v2, r2);
-      s[i2] = s2;
-      double w2 = (double)s2;
-      if (!wid) w2 *= __ldg(a.w + i2);
-      acc[0] = fma(w2, w2, acc[0]);
-    }
-  }
-  block_sum<1, kBlock>(acc, sm, blk);
-  if (grid_sum(blk, 1, a.red, tot) && threadIdx.x == 0) {
-    const double mus = sqrt(tot[0]) / S->mu0;
-    S->mu_s = mus;
-    if (mus < S->tol) S->halfexit = 1;
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kBlock) bcg_k2b(BcgArgs<T> a) {
-  BcgState* S = a.S;
-  if (S->stop || S->halfexit) return;
-  __shared__ TileStage<T, kStageCap> stage[kWarpsPerBlock];
-  __shared__ double blk[2], tot[2];
-  double* sm = reinterpret_cast<double*>(stage);  // reduction scratch after the tile loop
-  const T* __restrict__ sv = a.s;
-  T* __restrict__ tout = a.t;
-  double acc[2] = {0.0, 0.0};
-  BCG_TILE_LOOP(a) {
-    const int i = tile * 32 + lane_id();
-    const T t = csr_tile_row<T, T, kStageCap>(a.rowptr, a.colidx, a.val, a.s, a.n, a.nnz, tile * 32,
-                                                stage[warp_id()], a.err);
-    if (i < a.n) {
-      tout[i] = t;
-      acc[0] = fma((double)t, (double)sv[i], acc[0]);
-      acc[1] = fma((double)t, (double)t, acc[1]);
-    }
-  }
-  block_sum<2, kBlock>(acc, sm, blk);
-  if (grid_sum(blk, 2, a.red, tot) && threadIdx.x == 0) {
-    if (*(volatile int*)a.err) {
-      S->stop = 1;
-    } else if (!(tot[1] > 0.0)) {
-      S->conv = GSK_BREAKDOWN;
-      S->stop = 1;
-    } else {
-      S->omega = tot[0] / tot[1];
-    }
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void bcg_k3_row(const BcgArgs<T>& a, int i, double alpha, double omega, bool wid,
-                                           double (&acc)[3]) {
-  const double s = (double)a.s[i];
-  const double x = fma(alpha, (double)a.p[i], (double)a.x[i]);
-  a.x[i] = (T)fma(omega, s, x);
-  const T r = (T)fma(-omega, (double)a.t[i], s);
-  a.r[i] = r;
-  const double rd = (double)r;
-  acc[0] = fma((double)a.rh[i], rd, acc[0]);
-  if (wid) {
-    acc[1] = fma(rd, rd, acc[1]);
-  } else {
-    const double wr = __ldg(a.w + i) * rd;
-    acc[1] = fma(wr, wr, acc[1]);
-    acc[2] = fma(rd, rd, acc[2]);
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kBlock) bcg_k3(BcgArgs<T> a) {
-  BcgState* S = a.S;
-  if (S->stop) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(a, a.h_if, 1u);
-    return;
-  }
-  const double alpha = S->alpha;
-  if (S->halfexit) {
-    for (int i = blockIdx.x * kBlock + threadIdx.x; i < a.n; i += gridDim.x * kBlock)
-      a.x[i] = (T)fma(alpha, (double)a.p[i], (double)a.x[i]);
-    if (grid_last(a.cnt) && threadIdx.x == 0) {
-      S->iters += 1;
-      S->mu_rec = S->mu_s;
-      S->check = 1;
-      set_cond(a, a.h_if, 1u);
-    }
-    return;
-  }
-  __shared__ double sm[3 * kBlock], blk[3], tot[3];
-  const double omega = S->omega;
-  const bool wid = S->w_identity;
-  double acc[3] = {0.0, 0.0, 0.0};
-  BCG_ROW2_LOOP(a) {
-    bcg_k3_row(a, i, alpha, omega, wid, acc);
-    if (i + stride_ < a.n) bcg_k3_row(a, i + stride_, alpha, omega, wid, acc);
-  }
-  block_sum<3, kBlock>(acc, sm, blk);
-  if (grid_sum(blk, 3, a.red, tot) && threadIdx.x == 0) {
-    S->iters += 1;
-    const double mur = sqrt(tot[1]) / S->mu0;
-    S->mu_rec = mur;
-    int check = 0, stop = 0;
-    if (mur < S->tol) {
-      check = 1;
-    } else if (omega == 0.0) {
-      S->conv = GSK_BREAKDOWN;
-      stop = 1;
-    } else {
-      const double rho1 = tot[0], rn = sqrt(wid ? tot[1] : tot[2]);
-      if (!(fabs(rho1) > S->brk * S->rhn * rn)) {
-        S->conv = GSK_BREAKDOWN;
-        stop = 1;
-      } else {
-        S->beta = (rho1 / S->rho) * (alpha / omega);
-        S->rho = rho1;
-      }
-    }
-    if (!check && !stop && S->iters >= S->maxit) {
-      S->conv = GSK_MAXIT;
-      stop = 1;
-    }
-    S->check = check;
-    S->stop = stop;
-    set_cond(a, a.h_if, (unsigned)(check | stop));
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kBlock) bcg_k4(BcgArgs<T> a) {
-  const BcgState* S = a.S;
-  if (S->check || S->stop) return;  // the graph's IF node already excludes this
-  const double beta = S->beta, omega = S->omega;
-  const T* __restrict__ r = a.r;
-  const T* __restrict__ v = a.v;
-  T* __restrict__ p = a.p;
-  BCG_ROW2_LOOP(a) {
-    const int i2 = i + stride_;
-    const bool two = i2 < a.n;
-    const double p1 = (double)p[i], v1 = (double)v[i], r1 = (double)r[i];
-    const double p2 = two ? (double)p[i2] : 0.0, v2 = two ? (double)v[i2] : 0.0, r2 = two ? (double)r[i2] : 0.0;
-    p[i] = (T)fma(beta, fma(-omega, v1, p1), r1);
-    if (two) p[i2] = (T)fma(beta, fma(-omega, v2, p2), r2);
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(a, a.h_while, 1u);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kBlock) bcg_kt(BcgArgs<T> a) {
-  BcgState* S = a.S;
-  if (!(S->check || S->stop)) return;  // the graph's IF node already excludes this
-  __shared__ TileStage<T, kStageCap> stage[kWarpsPerBlock];
-  __shared__ double blk[2], tot[2];
-  double* sm = reinterpret_cast<double*>(stage);  // reduction scratch after the tile loop
-  const bool wid = S->w_identity;
-  double acc[2] = {0.0, 0.0};
-  BCG_TILE_LOOP(a) {
-    const int i = tile * 32 + lane_id();
-    const T ax = csr_tile_row<T, T, kStageCap>(a.rowptr, a.colidx, a.val, a.x, a.n, a.nnz, tile * 32,
-                                                 stage[warp_id()], a.err);
-    if (i < a.n) {
-      const T t = a.b[i] - ax;
-      a.t[i] = t;
-      const double wt = wgt(a.w, wid, i) * (double)t;
-      acc[0] = fma(wt, wt, acc[0]);
-      acc[1] = fma((double)t, (double)t, acc[1]);
-    }
-  }
-  block_sum<2, kBlock>(acc, sm, blk);
-  if (grid_sum(blk, 2, a.red, tot) && threadIdx.x == 0) {
-    S->mu_true = sqrt(tot[0]) / S->mu0;
-    S->tt_true = tot[1];
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kBlock) bcg_kr(BcgArgs<T> a) {
-  BcgState* S = a.S;
-  const int stop = S->stop, check = S->check;
-  if (!(check || stop)) return;  // the graph's IF node already excludes this
-  const bool met = S->mu_true < S->tol;
-  const bool refresh = !stop && check && !met && S->refresh_left > 0 && *(volatile int*)a.err == 0;
-  if (refresh) {
-    for (int i = blockIdx.x * kBlock + threadIdx.x; i < a.n; i += gridDim.x * kBlock) {
-      const T t = a.t[i];
-      a.r[i] = t;
-      a.rh[i] = t;
-      a.p[i] = t;
-    }
-  }
-  if (grid_last(a.cnt) && threadIdx.x == 0) {
-    int active = 0;
-    if (!stop && check) {
-      if (met) {
-        S->conv = GSK_CONVERGED;
-      } else if (refresh) {
-        S->refresh_left -= 1;
-        S->refreshes += 1;
-        S->rho = S->tt_true;
-        S->rhn = sqrt(S->tt_true);
-        S->check = 0;
-        S->halfexit = 0;
-        if (S->iters >= S->maxit) {
-          S->conv = GSK_MAXIT;
-        } else {
-          active = 1;
-        }
-      } else {
-        S->conv = GSK_STAGNATED;
-      }
-    }
-    S->stop = !active;
-    S->active = active;
-    set_cond(a, a.h_while, (unsigned)active);
-  }
-}
 
 // ------------------------------------------------------------------ host
 

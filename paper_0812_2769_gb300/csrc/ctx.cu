@@ -103,7 +103,7 @@ void gsk_opts_default(gsk_opts* o) {
   o->weights = nullptr;
   o->inner_tol = 1e-5;
   o->inner_maxit = 0;
-  o->max_refinements = 50;
+  o->max_refinements = 0;
 }
 
 gsk_status gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, void* stream) {

@@ -33,6 +33,18 @@ struct GridRed {
   int maxgrid;         // launches using this site must have gridDim.x <= maxgrid
 };
 
+// Per-thread accumulation type: FP64 data is accumulated in FP64; FP32 data
+// (the inner solves of the mixed-precision path) in FP32, so that an FP32
+// kernel does no FP64 work per element.  Block and grid sums are FP64.
+template <typename T>
+struct AccOf {
+  using type = double;
+};
+template <>
+struct AccOf<float> {
+  using type = float;
+};
+
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
 
