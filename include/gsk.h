@@ -194,6 +194,32 @@ gsk_status gmres_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, i
 gsk_status bicgstab_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, double tol,
                           const gsk_opts* opts, gsk_info* info, void* stream);
 
+/*
+ * bicgstab_solve_batched -- GS(p) then Bi-CGSTAB (Sec. 2) on nsys independent
+ * systems in one persistent kernel launch: each thread block takes the next
+ * system from a work queue (largest first), scales it, solves it with
+ * block-level reductions and takes another.  A system's result does not
+ * depend on the rest of the batch (bit-identical alone and in any batch).
+ *   A       host array [nsys] of FP64 CSR descriptors (device data)
+ *   b, x    host arrays [nsys] of device pointers (FP64 [n_i]); x holds x0 on
+ *           entry and the solution on exit
+ *   p       host array [nsys]: GS(p_i) is applied in place to A[i] and b[i]
+ *           first (p_i >= 1 or INFINITY); NaN means no scaling; NULL = NaN for all
+ *   tol     stopping tolerance of the metric of Sec. 2.2 (GS(2)-scaled residual)
+ *   opts    maxit, refresh, metric; precision GSK_PREC_MIXED runs FP32 inner
+ *           solves (relative tolerance inner_tol, at most inner_maxit
+ *           iterations each, 40 when 0) in FP64 refinement; a system whose
+ *           refinement step gains less than 10x in the FP64 metric is
+ *           finished by FP64 Bi-CGSTAB from its current x
+ *   infos   host array [nsys] or NULL; status host array [nsys] or NULL
+ *           (per-system gsk_status: GSK_ERR_ZERO_ROW / NONFINITE / ARG).
+ * When infos or status is given the call synchronises `stream`; it returns
+ * the first failing system's status (the others are still solved).
+ */
+gsk_status bicgstab_solve_batched(gsk_ctx* ctx, int nsys, const gsk_csr* A, void* const* b, void* const* x,
+                                  const double* p, double tol, const gsk_opts* opts, gsk_info* infos,
+                                  int32_t* status, void* stream);
+
 /* One timed kernel launch of gsk_profile_solve. */
 typedef struct {
   int32_t kernel;  /* kernel id, named by gsk_kernel_name */

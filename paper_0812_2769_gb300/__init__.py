@@ -85,6 +85,9 @@ SIGNATURES = {
                         C.POINTER(OptsC), C.POINTER(InfoC), C.c_void_p], C.c_int),
     "gsk_workspace_bytes": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)], C.c_int),
     "gsk_kernel_name": ([C.c_int], C.c_char_p),
+    "bicgstab_solve_batched": ([C.c_void_p, C.c_int, C.POINTER(CsrC), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                C.POINTER(C.c_double), C.c_double, C.POINTER(OptsC), C.POINTER(InfoC),
+                                C.POINTER(C.c_int32), C.c_void_p], C.c_int),
     "gsk_profile_solve": ([C.c_void_p, C.c_int, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                            C.POINTER(OptsC), C.c_int, C.POINTER(LaunchRecordC), C.c_int, C.POINTER(C.c_int),
                            C.POINTER(InfoC), C.c_void_p], C.c_int),
@@ -266,6 +269,30 @@ def bicgstab_solve(A: Csr, b, x, tol: float = 1e-8, options: OptsC | None = None
     ctx.check(lib().bicgstab_solve(ctx.handle, C.byref(Ac), _ptr(b), _ptr(x), float(tol), C.byref(o),
                                    C.byref(info) if sync else None, _stream_ptr(stream)))
     return info.as_dict() if sync else None
+
+
+def bicgstab_solve_batched(As, bs, xs, p=2.0, tol: float = 1e-8, options: OptsC | None = None,
+                           ctx: Context | None = None, stream=None, sync: bool = True, check: bool = True):
+    """GS(p) + Bi-CGSTAB on many systems in one persistent launch.  As: list of
+    Csr; bs, xs: lists of device tensors; p: one value or a list (NaN = no
+    scaling).  Returns (list of info dicts, list of statuses) when sync."""
+    n = len(As)
+    ctx = ctx or default_context(As[0].val.device.index or 0 if n else 0)
+    arr = (CsrC * n)(*[A.c() for A in As])
+    bp = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    pv = [p] * n if not isinstance(p, (list, tuple)) else list(p)
+    pa = (C.c_double * n)(*[float(v) for v in pv])
+    infos = (InfoC * n)() if sync else None
+    stat = (C.c_int32 * n)() if sync else None
+    o = options if options is not None else opts()
+    st = lib().bicgstab_solve_batched(ctx.handle, n, arr, bp, xp, pa, float(tol), C.byref(o), infos, stat,
+                                      _stream_ptr(stream))
+    if check and st != OK:
+        ctx.check(st)
+    if not sync:
+        return None
+    return [i.as_dict() for i in infos], list(stat)
 
 
 def profile_solve(A: Csr, b, x, solver: str = "bicgstab", m: int = 30, tol: float = 1e-8,

@@ -1,0 +1,546 @@
+// Batched persistent solver: many independent sparse systems in one launch.
+//
+// Each thread block takes the next system from an atomic work queue (systems
+// ordered largest first, so the tail of the batch is made of small ones),
+// applies GS(p) to it in place (Sec. 2, Eq. (2)), solves it with Bi-CGSTAB
+// (Sec. 2) using only block-level reductions, writes x and the outcome, and
+// takes the next system.  There is no grid-wide synchronisation and no
+// waiting on other blocks.  A system's arithmetic depends only on the system
+// and the block size, so its result is bit-identical alone and in any batch.
+//
+// Two precisions (template MIXED):
+//   FP64   Bi-CGSTAB as bicgstab_solve: recursive residual, true-residual
+//          confirmation and up to `refresh` restarts, breakdown tests.
+//   mixed  FP64 refinement around FP32 Bi-CGSTAB solves of (W2 A)_32 d =
+//          W2 r / ||W2 r|| to a relative tolerance inner_tol (W2 = GS(2)
+//          scales of the scaled matrix), x += ||W2 r|| d, as mixed.cu.  A
+//          system on which one refinement step gains less than 10x in the FP64
+//          metric (FP32 too coarse for its conditioning) is finished in FP64
+//          from its current x.
+// Per-block scratch vectors live in global memory (L2-resident while the
+// block works on its system).
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <numeric>
+
+#include "internal.hpp"
+
+namespace gsk {
+
+constexpr int kBatchBlock = 256;
+// mixed precision: FP32 iterations per refinement step when inner_maxit is 0
+// (short inner solves let the FP64 refinement and the escalation test act
+// early on systems whose conditioning is too much for FP32)
+constexpr int kBatchInnerMaxit = 40;
+
+struct BatchSys {
+  int n, nnz;
+  const int* rowptr;
+  const int* colidx;
+  double* val;
+  double* b;
+  double* x;
+  double p;  // GS(p) applied first; NaN = none
+};
+
+struct BatchOut {
+  int iters, refreshes, refinements, conv, status;
+  double relres_true, relres_rec;
+};
+
+struct BatchParams {
+  const BatchSys* sys;
+  const int* order;
+  int nsys;
+  unsigned* queue;
+  BatchOut* out;
+  char* scratch;
+  long long slot_bytes;
+  double tol, inner_tol, brk;
+  int maxit, refresh, inner_maxit, metric_plain;
+};
+
+template <int NV>
+__device__ __forceinline__ void bsum(const double (&v)[NV], double* sm, double* res) {
+  block_sum<NV, kBatchBlock>(v, sm, res);
+}
+
+// y = A x for one system, thread per row; bad indices flag *err.
+template <typename T>
+__device__ __forceinline__ void block_spmv(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+                                           const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y,
+                                           int* err) {
+  using Acc = typename AccOf<T>::type;
+  for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+    const int rs = rowptr[i], re = rowptr[i + 1];
+    Acc sum = Acc(0);
+    for (int k = rs; k < re; ++k) {
+      const int c = colidx[k];
+      if ((unsigned)c < (unsigned)n) sum = fma((Acc)val[k], (Acc)x[c], sum);
+      else *err = 1;
+    }
+    y[i] = (T)sum;
+  }
+}
+
+// Bi-CGSTAB on one system, block-local.  x holds the initial guess on entry.
+// confirm: FP64 mode (true residual check and refresh); otherwise an inner
+// solve stopped by the recursive residual relative to ||rhs||.
+// restart_on_breakdown (used only when a mixed-precision system is finished
+// in FP64): a breakdown restarts from the true residual while refreshes are
+// left, instead of ending the solve.
+template <typename T>
+__device__ void block_bicgstab(int n, const int* rowptr, const int* colidx, const T* val, const T* rhs, T* x,
+                               T* r, T* rh, T* p, T* v, T* s, T* t, const double* w, double tol, int maxit,
+                               int refresh, bool confirm, double brk, double* sm, int* err, BatchOut& o,
+                               bool restart_on_breakdown = false) {
+  using Acc = typename AccOf<T>::type;
+  __shared__ double res[4];
+  const bool wid = (w == nullptr);
+  // r = rhs - A x
+  block_spmv(n, rowptr, colidx, val, x, t, err);
+  __syncthreads();
+  double acc2[2] = {0.0, 0.0};
+  {
+    Acc a0 = 0, a1 = 0;
+    for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+      const T ri = (T)((Acc)rhs[i] - (Acc)t[i]);
+      r[i] = ri;
+      rh[i] = ri;
+      p[i] = ri;
+      const Acc wr = (Acc)(wid ? 1.0 : w[i]) * (Acc)ri;
+      a0 = fma(wr, wr, a0);
+      a1 = fma((Acc)ri, (Acc)ri, a1);
+    }
+    acc2[0] = a0;
+    acc2[1] = a1;
+  }
+  bsum<2>(acc2, sm, res);
+  const double mu0 = sqrt(res[0]);
+  double rho = res[1], rhn = sqrt(res[1]);
+  o.iters = 0;
+  o.refreshes = 0;
+  o.relres_rec = 1.0;
+  o.relres_true = 1.0;
+  o.conv = GSK_MAXIT;
+  if (!(mu0 > 0.0)) {
+    if (mu0 == 0.0) {
+      o.conv = GSK_CONVERGED;
+      o.relres_true = o.relres_rec = 0.0;
+    }
+    return;
+  }
+  int refresh_left = refresh;
+  bool broke = false;
+#define BCG_BREAKDOWN                                  \
+  {                                                    \
+    if (restart_on_breakdown && refresh_left > 0) {    \
+      broke = true;                                    \
+      check_true = true;                               \
+      break;                                           \
+    }                                                  \
+    o.conv = GSK_BREAKDOWN;                            \
+    goto done;                                         \
+  }
+  for (;;) {
+    bool check_true = false;
+    broke = false;
+    while (!check_true) {
+      if (o.iters >= maxit) {
+        o.conv = GSK_MAXIT;
+        goto done;
+      }
+      block_spmv(n, rowptr, colidx, val, p, v, err);
+      __syncthreads();
+      {
+        Acc a0 = 0, a1 = 0;
+        for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+          a0 = fma((Acc)rh[i], (Acc)v[i], a0);
+          a1 = fma((Acc)v[i], (Acc)v[i], a1);
+        }
+        double ad[2] = {(double)a0, (double)a1};
+        bsum<2>(ad, sm, res);
+      }
+      const double sigma = res[0], vn = sqrt(res[1]);
+      if (!(fabs(sigma) > brk * rhn * vn)) BCG_BREAKDOWN
+      const double alpha = rho / sigma;
+      {
+        Acc a0 = 0;
+        for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+          const T si = (T)fma(-(Acc)alpha, (Acc)v[i], (Acc)r[i]);
+          s[i] = si;
+          const Acc ws = (Acc)(wid ? 1.0 : w[i]) * (Acc)si;
+          a0 = fma(ws, ws, a0);
+        }
+        double ad[1] = {(double)a0};
+        bsum<1>(ad, sm, res);
+      }
+      const double mus = sqrt(res[0]) / mu0;
+      if (mus < tol) {
+        for (int i = threadIdx.x; i < n; i += kBatchBlock) x[i] = (T)fma((Acc)alpha, (Acc)p[i], (Acc)x[i]);
+        o.iters += 1;
+        o.relres_rec = mus;
+        check_true = true;
+        break;
+      }
+      block_spmv(n, rowptr, colidx, val, s, t, err);
+      __syncthreads();
+      {
+        Acc a0 = 0, a1 = 0;
+        for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+          a0 = fma((Acc)t[i], (Acc)s[i], a0);
+          a1 = fma((Acc)t[i], (Acc)t[i], a1);
+        }
+        double ad[2] = {(double)a0, (double)a1};
+        bsum<2>(ad, sm, res);
+      }
+      if (!(res[1] > 0.0)) BCG_BREAKDOWN
+      const double omega = res[0] / res[1];
+      {
+        Acc a0 = 0, a1 = 0, a2 = 0;
+        for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+          const Acc si = (Acc)s[i];
+          x[i] = (T)fma((Acc)omega, si, fma((Acc)alpha, (Acc)p[i], (Acc)x[i]));
+          const T ri = (T)fma(-(Acc)omega, (Acc)t[i], si);
+          r[i] = ri;
+          const Acc rd = (Acc)ri, wr = (Acc)(wid ? 1.0 : w[i]) * rd;
+          a0 = fma((Acc)rh[i], rd, a0);
+          a1 = fma(wr, wr, a1);
+          a2 = fma(rd, rd, a2);
+        }
+        double ad[3] = {(double)a0, (double)a1, (double)a2};
+        bsum<3>(ad, sm, res);
+      }
+      o.iters += 1;
+      const double mur = sqrt(res[1]) / mu0;
+      o.relres_rec = mur;
+      if (mur < tol) {
+        check_true = true;
+        break;
+      }
+      if (omega == 0.0) BCG_BREAKDOWN
+      const double rho1 = res[0], rn = sqrt(res[2]);
+      if (!(fabs(rho1) > brk * rhn * rn)) BCG_BREAKDOWN
+      const double beta = (rho1 / rho) * (alpha / omega);
+      rho = rho1;
+      for (int i = threadIdx.x; i < n; i += kBatchBlock)
+        p[i] = (T)fma((Acc)beta, fma(-(Acc)omega, (Acc)v[i], (Acc)p[i]), (Acc)r[i]);
+      __syncthreads();
+    }
+    if (!confirm) {  // inner solve: the recursive residual decides
+      o.conv = GSK_CONVERGED;
+      return;
+    }
+    // true residual
+    __syncthreads();
+    block_spmv(n, rowptr, colidx, val, x, t, err);
+    __syncthreads();
+    {
+      Acc a0 = 0, a1 = 0;
+      for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+        const T ti = (T)((Acc)rhs[i] - (Acc)t[i]);
+        t[i] = ti;
+        const Acc wt = (Acc)(wid ? 1.0 : w[i]) * (Acc)ti;
+        a0 = fma(wt, wt, a0);
+        a1 = fma((Acc)ti, (Acc)ti, a1);
+      }
+      double ad[2] = {(double)a0, (double)a1};
+      bsum<2>(ad, sm, res);
+    }
+    const double mu = sqrt(res[0]) / mu0;
+    o.relres_true = mu;
+    if (mu < tol) {
+      o.conv = GSK_CONVERGED;
+      return;
+    }
+    if (refresh_left == 0) {
+      o.conv = broke ? GSK_BREAKDOWN : GSK_STAGNATED;
+      return;
+    }
+    refresh_left -= 1;
+    o.refreshes += 1;
+    for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+      r[i] = t[i];
+      rh[i] = t[i];
+      p[i] = t[i];
+    }
+    rho = res[1];
+    rhn = sqrt(res[1]);
+    __syncthreads();
+  }
+#undef BCG_BREAKDOWN
+done:
+  if (confirm) {  // report the true metric of the returned x
+    __syncthreads();
+    block_spmv(n, rowptr, colidx, val, x, t, err);
+    __syncthreads();
+    Acc a0 = 0;
+    for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+      const Acc wt = (Acc)(wid ? 1.0 : w[i]) * ((Acc)rhs[i] - (Acc)t[i]);
+      a0 = fma(wt, wt, a0);
+    }
+    double ad[1] = {(double)a0};
+    bsum<1>(ad, sm, res);
+    o.relres_true = sqrt(res[0]) / mu0;
+  }
+}
+
+// GS(p) of one system in place (norms first, then the scaling only if no
+// row is zero or non-finite); then the metric weights W2 = 1/||a_i||_2 of the
+// scaled rows into w2 (left unused when p = 2: the rows then have unit norm).
+// Returns false (and the status) on an input error.
+__device__ bool block_gs(const BatchSys& S, double* d, double* w2, bool need_w2, int* status) {
+  __shared__ int s_err;
+  if (threadIdx.x == 0) s_err = 0;
+  __syncthreads();
+  const bool scale = !(S.p != S.p);
+  const int pm = scale ? pmode_of(S.p) : kP2;
+  for (int i = threadIdx.x; i < S.n; i += kBatchBlock) {
+    const int rs = S.rowptr[i], re = S.rowptr[i + 1];
+    if (rs < 0 || re < rs || re > S.nnz) {
+      atomicOr(&s_err, kErrIndex);
+      continue;
+    }
+    if (scale) d[i] = 1.0 / row_norm(S.val + rs, re - rs, pm, S.p, &s_err);
+    const unsigned long long bb = (unsigned long long)__double_as_longlong(S.b[i]);
+    if ((bb & 0x7ff0000000000000ull) == 0x7ff0000000000000ull) atomicOr(&s_err, kErrNonFinite);
+  }
+  __syncthreads();
+  if (s_err) {
+    *status = (s_err & kErrIndex) ? GSK_ERR_ARG : ((s_err & kErrNonFinite) ? GSK_ERR_NONFINITE : GSK_ERR_ZERO_ROW);
+    return false;
+  }
+  for (int i = threadIdx.x; i < S.n; i += kBatchBlock) {
+    const int rs = S.rowptr[i], re = S.rowptr[i + 1];
+    if (scale) {
+      const double di = d[i];
+      for (int k = rs; k < re; ++k) S.val[k] *= di;
+      S.b[i] *= di;
+    }
+    if (need_w2) w2[i] = 1.0 / row_norm(S.val + rs, re - rs, kP2, 2.0, &s_err);
+  }
+  __syncthreads();
+  if (s_err) {
+    *status = GSK_ERR_ZERO_ROW;
+    return false;
+  }
+  return true;
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kBatchBlock) batch_bicgstab(BatchParams P) {
+  __shared__ double sm[3 * kBatchBlock];
+  __shared__ int s_idx, s_err;
+  char* slot = P.scratch + (long long)blockIdx.x * P.slot_bytes;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_idx = (int)atomicAdd(P.queue, 1u);
+      s_err = 0;
+    }
+    __syncthreads();
+    if (s_idx >= P.nsys) break;
+    const int id = P.order[s_idx];
+    const BatchSys S = P.sys[id];
+    BatchOut o = {0, 0, 0, GSK_MAXIT, GSK_OK, 1.0, 1.0};
+    const int n = S.n;
+    double* d = reinterpret_cast<double*>(slot);
+    double* w2 = d + n;
+    // after GS(2) the rows have unit norm: the metric weights are the identity
+    const bool w_identity = P.metric_plain || S.p == 2.0;
+    const bool ok = block_gs(S, d, w2, !w_identity || MIXED, &o.status);
+    if (ok) {
+      if (!MIXED) {
+        double* v = w2 + n;
+        block_bicgstab<double>(n, S.rowptr, S.colidx, S.val, S.b, S.x, v, v + n, v + 2 * n, v + 3 * n, v + 4 * n,
+                               v + 5 * n, w_identity ? nullptr : w2, P.tol, P.maxit, P.refresh, true, P.brk, sm,
+                               &s_err, o);
+      } else {
+        // FP64 refinement around FP32 solves of (W2 A)_32 d = W2 r / ||W2 r||;
+        // a system whose refinement step gains less than 10x in the FP64 metric
+        // is finished by FP64 Bi-CGSTAB from its current x (escalation)
+        double* v64 = w2 + n;        // 6n doubles for the FP64 finish
+        double* r64 = v64 + 6 * n;
+        float* a32 = reinterpret_cast<float*>(r64 + n);
+        float* f = a32 + ((S.nnz + 3) / 4) * 4;
+        float *x32 = f, *r = f + n, *rh = f + 2 * n, *p = f + 3 * n, *v = f + 4 * n, *s = f + 5 * n,
+              *t = f + 6 * n, *rhs = f + 7 * n;
+        __shared__ double res[2];
+        for (int i = threadIdx.x; i < n; i += kBatchBlock)
+          for (int k = S.rowptr[i]; k < S.rowptr[i + 1]; ++k) a32[k] = (float)(S.val[k] * w2[i]);
+        double mu0 = -1.0, mu_prev = 1.0;
+        int total = 0;
+        for (int ref = 0;; ++ref) {
+          __syncthreads();
+          block_spmv<double>(n, S.rowptr, S.colidx, S.val, S.x, r64, &s_err);
+          __syncthreads();
+          double a0 = 0.0, a1 = 0.0;
+          for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+            const double ri = S.b[i] - r64[i];
+            r64[i] = ri;
+            const double wr = (w_identity ? 1.0 : w2[i]) * ri, w2r = w2[i] * ri;
+            a0 = fma(wr, wr, a0);
+            a1 = fma(w2r, w2r, a1);
+          }
+          double ad[2] = {a0, a1};
+          bsum<2>(ad, sm, res);
+          const double mw = sqrt(res[0]), rn = sqrt(res[1]);
+          if (ref == 0) mu0 = mw;
+          o.refinements = ref;
+          if (!(mu0 > 0.0)) {
+            o.conv = mu0 == 0.0 ? GSK_CONVERGED : GSK_MAXIT;
+            o.relres_true = mu0 == 0.0 ? 0.0 : 1.0;
+            break;
+          }
+          const double mu = mw / mu0;
+          o.relres_true = mu;
+          if (mu < P.tol) {
+            o.conv = GSK_CONVERGED;
+            break;
+          }
+          if (total >= P.maxit || !(mu == mu)) {
+            o.conv = GSK_MAXIT;
+            break;
+          }
+          bool escalate = ref > 0 && mu > 0.1 * mu_prev;
+          if (!escalate) {
+            mu_prev = mu;
+            const double inv = 1.0 / rn;
+            for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+              rhs[i] = (float)(w2[i] * r64[i] * inv);
+              x32[i] = 0.f;
+            }
+            __syncthreads();
+            BatchOut oi = {0, 0, 0, GSK_MAXIT, GSK_OK, 1.0, 1.0};
+            block_bicgstab<float>(n, S.rowptr, S.colidx, a32, rhs, x32, r, rh, p, v, s, t, nullptr, P.inner_tol,
+                                  min(P.inner_maxit, P.maxit - total), 0, false, P.brk, sm, &s_err, oi);
+            total += oi.iters;
+            o.relres_rec = oi.relres_rec;
+            __syncthreads();
+            // a correction that is not finite, or an inner solve that made no
+            // step, is not applied: the system goes to FP64 instead
+            int bad = oi.iters == 0;
+            for (int i = threadIdx.x; i < n; i += kBatchBlock) bad |= !isfinite(x32[i]);
+            escalate = __syncthreads_or(bad) != 0;
+            if (!escalate) {
+              for (int i = threadIdx.x; i < n; i += kBatchBlock) S.x[i] = fma(rn, (double)x32[i], S.x[i]);
+              continue;
+            }
+          }
+          // escalate: FP64 Bi-CGSTAB on the remaining error, the tolerance
+          // rescaled so that it is still relative to the first residual
+          BatchOut o64 = {0, 0, 0, GSK_MAXIT, GSK_OK, 1.0, 1.0};
+          block_bicgstab<double>(n, S.rowptr, S.colidx, S.val, S.b, S.x, v64, v64 + n, v64 + 2 * n, v64 + 3 * n,
+                                 v64 + 4 * n, v64 + 5 * n, w_identity ? nullptr : w2, P.tol / mu, P.maxit - total,
+                                 P.refresh > 10 ? P.refresh : 10, true, P.brk, sm, &s_err, o64, true);
+          total += o64.iters;
+          o.conv = o64.conv;
+          o.refreshes = o64.refreshes;
+          o.relres_true = o64.relres_true * mu;
+          o.relres_rec = o64.relres_rec * mu;
+          o.refinements = ref + 1;
+          break;
+        }
+        o.iters = total;
+      }
+    }
+    __syncthreads();
+    if (s_err) o.status = GSK_ERR_ARG;
+    if (threadIdx.x == 0) P.out[id] = o;
+  }
+}
+
+static size_t batch_slot_bytes(bool mixed, int nmax, int nnzmax) {
+  // FP64: d, w2, six vectors.  Mixed: d, w2, six FP64 vectors (escalation),
+  // the FP64 residual, (W2 A)_32 and eight FP32 vectors.
+  size_t b = mixed ? (9 * 8 * (size_t)nmax + 4 * ((size_t)(nnzmax + 3) / 4 * 4) + 8 * 4 * (size_t)nmax)
+                   : 8 * 8 * (size_t)nmax;
+  return (b + 255) / 256 * 256;
+}
+
+}  // namespace gsk
+
+using namespace gsk;
+
+extern "C" gsk_status bicgstab_solve_batched(gsk_ctx* ctx, int nsys, const gsk_csr* A, void* const* b,
+                                             void* const* x, const double* p, double tol, const gsk_opts* opts_in,
+                                             gsk_info* infos, int32_t* status, void* stream) {
+  if (!ctx) return GSK_ERR_ARG;
+  if (nsys < 0 || (nsys > 0 && (!A || !b || !x))) return ctx->fail(GSK_ERR_ARG, "bad batch arrays");
+  gsk_opts opts;
+  if (opts_in) opts = *opts_in;
+  else gsk_opts_default(&opts);
+  if (!(tol >= 0.0) || opts.maxit < 0 || opts.refresh < 0 || !(opts.inner_tol > 0.0) || opts.inner_maxit < 0)
+    return ctx->fail(GSK_ERR_ARG, "bad tol/maxit/refresh/inner_tol");
+  if (opts.weights) return ctx->fail(GSK_ERR_ARG, "the batched solver derives its metric weights itself");
+  if (nsys == 0) return GSK_OK;
+  const bool mixed = opts.precision == GSK_PREC_MIXED;
+  std::vector<BatchSys> hs(nsys);
+  int nmax = 0, nnzmax = 0;
+  for (int i = 0; i < nsys; ++i) {
+    gsk_status s = check_csr(ctx, &A[i]);
+    if (s != GSK_OK) return s;
+    if (A[i].dtype != GSK_F64) return ctx->fail(GSK_ERR_ARG, "batched systems must be FP64");
+    if (A[i].n > 0 && (!b[i] || !x[i])) return ctx->fail(GSK_ERR_ARG, "NULL b or x in the batch");
+    const double pi = p ? p[i] : NAN;
+    if (!(pi != pi) && !(pi >= 1.0)) return ctx->fail(GSK_ERR_ARG, "p must be >= 1, INFINITY or NaN");
+    hs[i] = BatchSys{A[i].n, A[i].nnz, A[i].rowptr, A[i].colidx, (double*)A[i].val, (double*)b[i], (double*)x[i], pi};
+    nmax = std::max(nmax, A[i].n);
+    nnzmax = std::max(nnzmax, A[i].nnz);
+  }
+  // largest systems first
+  std::vector<int> order(nsys);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return hs[a].nnz > hs[c].nnz; });
+
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, mixed ? batch_bicgstab<true> : batch_bicgstab<false>, kBatchBlock, 0);
+  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+  const int grid = std::max(1, std::min(nsys, ctx->num_sms * per_sm));
+  const size_t slot = batch_slot_bytes(mixed, nmax, nnzmax);
+
+  Arena sizing;
+  sizing.take<unsigned>(64);
+  sizing.take<BatchSys>(nsys);
+  sizing.take<int>(nsys);
+  sizing.take<BatchOut>(nsys);
+  sizing.take<char>(slot * grid);
+  gsk_status s = ctx->reserve(sizing.off);
+  if (s != GSK_OK) return s;
+  Arena ar{(char*)ctx->ws, ctx->ws_bytes, 0};
+  unsigned* queue = ar.take<unsigned>(64);
+  BatchSys* dsys = ar.take<BatchSys>(nsys);
+  int* dorder = ar.take<int>(nsys);
+  BatchOut* dout = ar.take<BatchOut>(nsys);
+  char* scratch = ar.take<char>(slot * grid);
+
+  cudaStream_t st = (cudaStream_t)stream;
+  GSK_CK(cudaEventRecord(ctx->ev0, st));
+  GSK_CK(cudaMemsetAsync(queue, 0, sizeof(unsigned), st));
+  GSK_CK(cudaMemcpyAsync(dsys, hs.data(), sizeof(BatchSys) * nsys, cudaMemcpyHostToDevice, st));
+  GSK_CK(cudaMemcpyAsync(dorder, order.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+  BatchParams P{dsys, dorder, nsys, queue, dout, scratch, (long long)slot, tol, opts.inner_tol,
+                1e-16 * DBL_EPSILON, opts.maxit, opts.refresh,
+                opts.inner_maxit > 0 ? opts.inner_maxit : kBatchInnerMaxit, opts.metric == GSK_METRIC_PLAIN ? 1 : 0};
+  if (mixed) batch_bicgstab<true><<<grid, kBatchBlock, 0, st>>>(P);
+  else batch_bicgstab<false><<<grid, kBatchBlock, 0, st>>>(P);
+  GSK_CK(cudaGetLastError());
+  GSK_CK(cudaEventRecord(ctx->ev1, st));
+  if (!infos && !status) return GSK_OK;
+  std::vector<BatchOut> ho(nsys);
+  GSK_CK(cudaMemcpyAsync(ho.data(), dout, sizeof(BatchOut) * nsys, cudaMemcpyDeviceToHost, st));
+  GSK_CK(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+  gsk_status worst = GSK_OK;
+  for (int i = 0; i < nsys; ++i) {
+    if (infos) infos[i] = gsk_info{ho[i].iters, 0, ho[i].refreshes, ho[i].refinements, ho[i].conv, ho[i].relres_true,
+                                   ho[i].relres_rec, ms};
+    if (status) status[i] = ho[i].status;
+    if (ho[i].status != GSK_OK && worst == GSK_OK) worst = (gsk_status)ho[i].status;
+  }
+  if (worst != GSK_OK) return ctx->fail(worst, "at least one system of the batch failed (see status[])");
+  return GSK_OK;
+}

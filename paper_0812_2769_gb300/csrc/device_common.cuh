@@ -199,6 +199,66 @@ __device__ __forceinline__ bool grid_last(unsigned* counter) {
   return s_last;
 }
 
+// ------------------------------------------------------------- row norms
+
+enum PMode : int { kP1 = 0, kP2 = 1, kPInf = 2, kPGen = 3 };
+
+__host__ __device__ inline int pmode_of(double p) {
+  return p == 1.0 ? kP1 : (p == 2.0 ? kP2 : (p > 1e300 ? kPInf : kPGen));
+}
+
+// ||a||_p of one row held in shared memory (values converted to double).
+// p = 2 sums squares directly unless the largest magnitude is near the ends
+// of the exponent range, where the row is first scaled by an exact power of
+// two; this is the definition up to rounding.  The largest magnitude and the
+// finiteness test use the integer bit patterns (no FP64 work).
+template <typename T>
+__device__ __forceinline__ double row_norm(const T* v, int len, int pmode, double p, int* err) {
+  unsigned long long mb = 0ull;
+  bool nonfinite = false;
+  for (int k = 0; k < len; ++k) {
+    unsigned long long bits = (unsigned long long)__double_as_longlong((double)v[k]) & 0x7fffffffffffffffull;
+    nonfinite |= bits >= 0x7ff0000000000000ull;
+    mb = bits > mb ? bits : mb;
+  }
+  if (nonfinite) {
+    atomicOr(err, kErrNonFinite);
+    return 1.0;
+  }
+  if (mb == 0ull) {
+    atomicOr(err, kErrZeroRow);
+    return 1.0;
+  }
+  const double m = __longlong_as_double((long long)mb);
+  if (pmode == kPInf) return m;
+  if (pmode == kP1) {
+    double s = 0.0;
+    for (int k = 0; k < len; ++k) s += fabs((double)v[k]);
+    return s;
+  }
+  if (pmode == kP2) {
+    const int e = (int)(mb >> 52) - 1023;
+    if (e > -480 && e < 480) {
+      double s = 0.0;
+      for (int k = 0; k < len; ++k) {
+        const double a = (double)v[k];
+        s = fma(a, a, s);
+      }
+      return sqrt(s);
+    }
+    const double sc = ldexp(1.0, -e), isc = ldexp(1.0, e);
+    double s = 0.0;
+    for (int k = 0; k < len; ++k) {
+      const double a = (double)v[k] * sc;
+      s = fma(a, a, s);
+    }
+    return sqrt(s) * isc;
+  }
+  double s = 0.0;
+  for (int k = 0; k < len; ++k) s += pow(fabs((double)v[k]) / m, p);
+  return m * pow(s, 1.0 / p);
+}
+
 // ------------------------------------------------------------- CSR tiles
 //
 // One warp computes the products of 32 consecutive rows r0..r0+31 with a
