@@ -59,7 +59,10 @@ typedef enum {
 
 typedef enum {
   GSK_PREC_F64 = 0,   /* every vector and product in FP64 */
-  GSK_PREC_MIXED = 1  /* FP32 inner Krylov solves inside FP64 iterative refinement */
+  GSK_PREC_MIXED = 1  /* FP32 inner Krylov solves inside FP64 iterative refinement;
+                         when a refinement step stops paying off (less than 10x
+                         for Bi-CGSTAB, no progress for a GMRES cycle) the solve
+                         is finished by the FP64 solver from the current x */
 } gsk_precision;
 
 typedef struct gsk_ctx gsk_ctx;

@@ -414,7 +414,8 @@ __global__ void __launch_bounds__(kBatchBlock) batch_bicgstab(BatchParams P) {
             __syncthreads();
             BatchOut oi = {0, 0, 0, GSK_MAXIT, GSK_OK, 1.0, 1.0};
             block_bicgstab<float>(n, S.rowptr, S.colidx, a32, rhs, x32, r, rh, p, v, s, t, nullptr, P.inner_tol,
-                                  min(P.inner_maxit, P.maxit - total), 0, false, P.brk, sm, &s_err, oi);
+                                  min(P.inner_maxit, P.maxit - total), 0, false, (double)FLT_EPSILON, sm, &s_err,
+                                  oi);
             total += oi.iters;
             o.relres_rec = oi.relres_rec;
             __syncthreads();

@@ -20,6 +20,14 @@
 // Graph: [weights, convert, residual] -> WHILE_outer{ prep -> inner solve ->
 // update -> residual }, the inner solve being the Bi-CGSTAB WHILE/IF body or
 // the GMRES Arnoldi WHILE body of the FP64 solvers instantiated for float.
+// A correction that is not finite is never applied.  A refinement step that
+// gains less than 10x (Bi-CGSTAB) or nothing (a GMRES cycle) ends the FP32
+// loop as STAGNATED: FP32 is too coarse for the system's conditioning, and the
+// solve is finished by the FP64 solver from the current x (one host decision,
+// only on that path), with the tolerance rescaled to the first residual.
+#include <cfloat>
+#include <cmath>
+
 #include "bicgstab_kernels.cuh"
 #include "gmres_kernels.cuh"
 #include "graph.hpp"
@@ -27,8 +35,8 @@
 namespace gsk {
 
 struct MxState {
-  double mu0, mu, rnorm, tol;
-  int refinements, max_ref, total_iters, maxit, conv, stop, w_identity, solver;
+  double mu0, mu, rnorm, tol, mu_prev, stag;
+  int refinements, max_ref, total_iters, maxit, conv, stop, w_identity, solver, skip, skipped;
 };
 
 struct MxArgs {
@@ -105,6 +113,7 @@ __global__ void __launch_bounds__(kBlock) mx_residual(MxArgs a) {
     if (INIT) {
       S->mu0 = mw;
       S->mu = 1.0;
+      S->mu_prev = 1.0;
       S->refinements = 0;
       S->total_iters = 0;
       S->conv = GSK_MAXIT;
@@ -134,7 +143,12 @@ __global__ void __launch_bounds__(kBlock) mx_residual(MxArgs a) {
                  !(mu == mu)) {
         S->conv = GSK_MAXIT;
         stop = 1;
+      } else if (mu > S->stag * S->mu_prev) {
+        // the FP32 step no longer gains enough: hand over to FP64 (host side)
+        S->conv = GSK_STAGNATED;
+        stop = 1;
       }
+      S->mu_prev = mu;
     }
     S->stop = stop;
     cudaGraphSetConditional(a.h_outer, (unsigned)!stop);
@@ -177,8 +191,23 @@ __global__ void mx_inner_finish(MxArgs a) {
   if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(a.h_inner, 0u);
 }
 
-// x += ||W2 r|| x32 (FP64).
+// Counts non-finite entries of the FP32 correction; a correction that is not
+// finite is not applied (S->skip), so x only ever takes finite steps.
+__global__ void __launch_bounds__(kBlock) mx_check_bcg(MxArgs a) {
+  __shared__ double sm[kBlock], blk[1], tot[1];
+  int bad = 0;
+  MX_ROW_LOOP(a) bad |= !isfinite(a.x32[i]);
+  const double accd[1] = {(double)bad};
+  block_sum<1, kBlock>(accd, sm, blk);
+  if (grid_sum(blk, 1, a.red, tot) && threadIdx.x == 0) {
+    a.S->skip = tot[0] != 0.0;
+    a.S->skipped += a.S->skip;
+  }
+}
+
+// x += ||W2 r|| x32 (FP64), unless the correction was not finite.
 __global__ void __launch_bounds__(kBlock) mx_update_bcg(MxArgs a) {
+  if (a.S->skip) return;
   const double s = a.S->rnorm;
   MX_ROW_LOOP(a) a.x[i] = fma(s, (double)a.x32[i], a.x[i]);
 }
@@ -220,6 +249,9 @@ __global__ void __launch_bounds__(kBlock) mx_update_gm(MxArgs a) {
   const double s = a.S->rnorm;
   for (int c = threadIdx.x; c < k; c += kBlock) coef[c] = s * a.sig[c] * a.y[c];
   __syncthreads();
+  // a least-squares solution that is not finite (singular H) is not applied
+  for (int c = 0; c < k; ++c)
+    if (!isfinite(coef[c])) return;
   MX_ROW_LOOP(a) {
     double x = a.x[i];
 #pragma unroll
@@ -325,6 +357,9 @@ static gsk_status mx_prepare(gsk_ctx* ctx, int solver, const gsk_csr* A, const v
   P.hs.max_ref = opts.max_refinements;
   P.hs.w_identity = P.wmode == 1 ? 1 : 0;
   P.hs.solver = solver;
+  // a refinement step must gain 10x (Bi-CGSTAB solve) or make some progress
+  // (one GMRES cycle) to continue in FP32
+  P.hs.stag = solver == 1 ? 0.1 : 0.99;
   const int inner_maxit = opts.inner_maxit > 0 ? opts.inner_maxit : (solver == 0 ? m : opts.maxit);
 
   if (solver == 1) {
@@ -349,7 +384,9 @@ static gsk_status mx_prepare(gsk_ctx* ctx, int solver, const gsk_csr* A, const v
     bi.in_graph = 1;
     std::memset(&P.hb, 0, sizeof(P.hb));
     P.hb.tol = opts.inner_tol;
-    P.hb.brk = 1e-16 * DBL_EPSILON;
+    // FP32 rounding noise swamps |<rh, v>| below about FLT_EPSILON ||rh|| ||v||:
+    // the inner solve stops there and the refinement restarts it
+    P.hb.brk = FLT_EPSILON;
     P.hb.maxit = inner_maxit;
     P.hb.w_identity = 1;
   } else {
@@ -467,6 +504,7 @@ static gsk_status mx_record(gsk_ctx* ctx, MxPlan& P, cudaGraphExec_t* exec_out) 
     GSK_CK(c3.end());
     Capture c4;
     GSK_CK(c4.begin(cs, obody, {inode}));
+    mx_check_bcg<<<P.g_vec, kBlock, 0, cs>>>(a);
     mx_update_bcg<<<P.g_vec, kBlock, 0, cs>>>(a);
     mx_residual<false><<<P.g_tile, kBlock, 0, cs>>>(a);
     GSK_CK(c4.end());
@@ -534,7 +572,27 @@ static gsk_status mx_solve(gsk_ctx* ctx, int solver, const gsk_csr* A, const voi
   *info = gsk_info{out.total_iters, (solver == 0 && out.refinements > 0) ? out.refinements - 1 : 0, 0,
                    out.refinements, out.conv, out.mu,
                    inner_rec, ms};
-  return err_bits_status(ctx, bits);
+  gsk_status st_bits = err_bits_status(ctx, bits);
+  if (st_bits != GSK_OK || out.conv != GSK_STAGNATED || !(out.mu > 0.0) || !std::isfinite(out.mu) ||
+      out.total_iters >= opts->maxit)
+    return st_bits;
+  // The refinement stopped short of tol (FP32 too coarse for this system):
+  // finish in FP64 from the current x, the tolerance rescaled so that it is
+  // still relative to the first residual.
+  gsk_opts o64 = *opts;
+  o64.precision = GSK_PREC_F64;
+  o64.maxit = opts->maxit - out.total_iters;
+  gsk_info i64;
+  gsk_status s64 = solver == 1 ? bicgstab_solve(ctx, A, b, x, tol / out.mu, &o64, &i64, stream)
+                               : gmres_solve(ctx, A, b, x, m, tol / out.mu, &o64, &i64, stream);
+  if (s64 != GSK_OK) return s64;
+  info->iters += i64.iters;
+  info->refreshes = i64.refreshes;
+  info->conv = i64.conv;
+  info->relres_true = i64.relres_true * out.mu;
+  info->relres_rec = i64.relres_rec * out.mu;
+  info->ms += i64.ms;
+  return GSK_OK;
 }
 
 }  // namespace gsk
