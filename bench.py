@@ -49,6 +49,10 @@ def parse_args(argv=None):
     ap.add_argument("--grid", type=int, default=N_GRID, help="grid side (128 = the benchmark workload)")
     ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel profiling pass")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the mixed-precision, batched (4096 systems) and serving measurements")
+    ap.add_argument("--batch", type=int, default=4096, help="systems in the batched measurement")
+    ap.add_argument("--serve-requests", type=int, default=120, help="requests in the serving measurement")
     return ap.parse_args(argv)
 
 
@@ -333,6 +337,12 @@ def run_gpu(args):
     if not args.no_cpu and rank == 0 and world == 1:
         cpu = cpu_sample(s)
 
+    extra = None
+    if not args.no_extra and rank == 0:
+        extra = {"mixed_precision": mixed_pass(g, ctx, A, val0, b, b0, x1, x2, args)}
+        extra["batched"] = batched_pass(g, args)
+        extra["serving"] = serving_pass(args)
+
     if rank == 0:
         i1, i2 = infos[-1]
         line = {
@@ -345,10 +355,112 @@ def run_gpu(args):
                        "gmres30": {k: i2[k] for k in ("iters", "restarts", "conv_name", "relres_true", "ms")},
                        "all_converged_below_tol": ok},
             "kernels": kernels,
+            "forms": extra,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def mixed_pass(g, ctx, A, val0, b, b0, x1, x2, args):
+    """The same step with the mixed-precision solvers (FP32 inner solves in
+    FP64 refinement; the FP64 metric still has to fall below 1e-8)."""
+    import torch
+
+    o = g.opts(precision=g.PREC_MIXED)
+
+    def step():
+        A.val.copy_(val0)
+        b.copy_(b0)
+        g.gs_scale(A, b, p=2.0, ctx=ctx)
+        x1.zero_()
+        i1 = g.bicgstab_solve(A, b, x1, tol=TOL, options=o, ctx=ctx)
+        x2.zero_()
+        i2 = g.gmres_solve(A, b, x2, m=M_GMRES, tol=TOL, options=o, ctx=ctx)
+        return i1, i2
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    K = max(1, args.steps)
+    e0.record()
+    infos = [step() for _ in range(K)]
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    i1, i2 = infos[-1]
+    return {"value": SOLVES_PER_STEP * K / t, "unit": UNIT, "ms_per_step": 1e3 * t / K, "dtype": "f32 inner, f64 refinement",
+            "bicgstab": {k: i1[k] for k in ("iters", "refinements", "conv_name", "relres_true", "ms")},
+            "gmres30": {k: i2[k] for k in ("iters", "refinements", "conv_name", "relres_true", "ms")},
+            "all_converged_below_tol": all(a["conv"] == 0 and a["relres_true"] < TOL and c["conv"] == 0
+                                           and c["relres_true"] < TOL for a, c in infos)}
+
+
+def batched_pass(g, args):
+    """The batch configuration: args.batch 2D inclusion systems (side 16..128),
+    GS(2) + Bi-CGSTAB to 1e-8 in one persistent launch, FP64 and mixed,
+    against a loop of single-system FP64 solves on the first 128 systems."""
+    import torch
+
+    from problems import configs
+
+    systems = [configs.c4_system(i) for i in range(args.batch)]
+    val0 = [torch.as_tensor(x.val, device="cuda") for x in systems]
+    b0 = [torch.as_tensor(x.b, device="cuda") for x in systems]
+    As = [g.Csr.from_host(x.rowptr, x.colidx, x.val) for x in systems]
+    bs = [v.clone() for v in b0]
+    xs = [torch.zeros(x.n, dtype=torch.float64, device="cuda") for x in systems]
+    ctx = g.Context(torch.cuda.current_device())
+    out = {"systems": len(systems), "unknowns": int(sum(x.n for x in systems)),
+           "nnz": int(sum(x.nnz for x in systems))}
+    for name, prec in (("f64", g.PREC_F64), ("mixed", g.PREC_MIXED)):
+        best = None
+        for _ in range(2):
+            for A, v, bb, b1, x in zip(As, val0, b0, bs, xs):
+                A.val.copy_(v)
+                b1.copy_(bb)
+                x.zero_()
+            torch.cuda.synchronize()
+            infos, _ = g.bicgstab_solve_batched(As, bs, xs, p=2.0, tol=TOL, options=g.opts(precision=prec), ctx=ctx)
+            ms = infos[0]["ms"]
+            best = ms if best is None else min(best, ms)
+        out[name] = {"value": len(systems) / (best / 1e3), "unit": UNIT, "ms": best,
+                     "converged": sum(i["conv"] == g.CONVERGED for i in infos),
+                     "iters_mean": float(sum(i["iters"] for i in infos) / len(infos))}
+    K = min(128, len(systems))
+    for A, v, bb, b1, x in zip(As[:K], val0[:K], b0[:K], bs[:K], xs[:K]):
+        A.val.copy_(v)
+        b1.copy_(bb)
+        x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for A, b1, x in zip(As[:K], bs[:K], xs[:K]):
+        g.gs_scale(A, b1, p=2.0, ctx=ctx)
+        g.bicgstab_solve(A, b1, x, tol=TOL, ctx=ctx)
+    torch.cuda.synchronize()
+    out["per_system_loop_f64"] = {"value": K / (time.perf_counter() - t0), "unit": UNIT, "systems": K}
+    return out
+
+
+def serving_pass(args):
+    """Serving: Poisson arrivals of mixed 2D/3D requests (see problems/serving.py),
+    mixed precision to 1e-8, p50/p99 latency and completed solves per second."""
+    from paper_0812_2769_gb300 import serve
+    from problems import serving as sv
+
+    rate = 10.0
+    specs = sv.stream(args.serve_requests, rate=rate, seed=7)
+    reqs = [serve.Request(sp.rid, sp.build(), solver=sp.solver, m=sp.m, p=sp.p, tol=TOL, precision="mixed",
+                          arrival=sp.arrival, maxit=3000) for sp in specs]
+    be = serve.GpuBackend(0, slots=6)
+    serve.Server(be, slots=6).run(reqs[:3], realtime=False)  # warm the contexts
+    srv = serve.Server(be, slots=6)
+    res = srv.run(reqs, realtime=True)
+    out = serve.summarize(res)
+    out.update({"arrival_rate_per_s": rate, "slots": 6, "peak_admitted_GB": round(srv.peak_in_use / 1e9, 3),
+                "maxit": 3000})
+    return out
 
 
 def profile_pass(g, ctx, A, val0, b, b0, s):
