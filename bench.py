@@ -53,6 +53,10 @@ def parse_args(argv=None):
                     help="skip the mixed-precision, batched (4096 systems) and serving measurements")
     ap.add_argument("--batch", type=int, default=4096, help="systems in the batched measurement")
     ap.add_argument("--serve-requests", type=int, default=120, help="requests in the serving measurement")
+    ap.add_argument("--profile-kernels", choices=["gmres", "bicgstab", "both"], default=None,
+                    help="only drive the solvers' kernels from a host loop on the workload (for ncu captures)")
+    ap.add_argument("--gmres-iters", type=int, default=30, help="Arnoldi steps in --profile-kernels")
+    ap.add_argument("--bicgstab-iters", type=int, default=20, help="Bi-CGSTAB iterations in --profile-kernels")
     return ap.parse_args(argv)
 
 
@@ -189,7 +193,7 @@ def kernel_cost(name, step, n, nnz):
         "bcg_kr_finish": (4 * V, 0),
         "gm_init_residual": (spmv_b + 3 * V, 2 * nnz + 4 * n),
         "gm_gr_restart_residual": (spmv_b + 3 * V, 2 * nnz + 4 * n),
-        "gm_ga_spmv": (spmv_b + 2 * V, 2 * nnz + 3 * n),
+        "gm_ga_spmv": (spmv_b + 2 * V, 2 * nnz + n),
         "gm_gd_cgs_pass1": ((k + 1) * V, 2 * k * n),
         "gm_gb_cgs_pass2": ((k + 2) * V, 4 * k * n),
         "gm_gc_cgs_pass3_givens": ((k + 2) * V, 2 * k * n + 2 * n),
@@ -563,8 +567,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_kernels(args):
+    """Kernel-only run for ncu: GS(2) on the workload, then the FP64 solvers'
+    kernels driven from a host loop for a fixed number of iterations."""
+    import torch
+
+    import paper_0812_2769_gb300 as g
+
+    s = workload(args.grid)
+    A = g.Csr.from_host(s.rowptr, s.colidx, s.val)
+    b = torch.as_tensor(s.b, device="cuda")
+    g.gs_scale(A, b, p=2.0)
+    for solver, iters in (("gmres", args.gmres_iters), ("bicgstab", args.bicgstab_iters)):
+        if args.profile_kernels in (solver, "both"):
+            x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+            recs, info = g.profile_solve(A, b, x, solver=solver, m=M_GMRES, tol=TOL, max_iters=iters)
+            print(solver, len(recs), "launches", info["iters"], "iterations")
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.profile_kernels:
+        profile_kernels(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

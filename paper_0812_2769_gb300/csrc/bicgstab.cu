@@ -8,7 +8,7 @@ namespace gsk {
 // ------------------------------------------------------------------ host
 
 struct BcgPlan {
-  int g_tile, g_vec, wmode;
+  int g_tile, g_k2a, g_k3, g_k4, wmode;
   BcgArgs<double> a;
   double* wbuf;  // weights computed by the solver (or nullptr)
   BcgState host_state;
@@ -21,12 +21,12 @@ static void bcg_launch(gsk_ctx* ctx, BcgPlan& P, int k, cudaStream_t s) {
     case kKUnitCheck: launch_unit_check(ctx, a.n, P.wbuf, a.red, &a.S->w_identity, s); break;
     case kKBcgInit: bcg_init<double><<<P.g_tile, kBlock, 0, s>>>(a); break;
     case kKBcgK1: bcg_k1<double><<<P.g_tile, kBlock, 0, s>>>(a); break;
-    case kKBcgK2a: bcg_k2a<double><<<P.g_vec, kBlock, 0, s>>>(a); break;
+    case kKBcgK2a: bcg_k2a<double><<<P.g_k2a, kBlock, 0, s>>>(a); break;
     case kKBcgK2b: bcg_k2b<double><<<P.g_tile, kBlock, 0, s>>>(a); break;
-    case kKBcgK3: bcg_k3<double><<<P.g_vec, kBlock, 0, s>>>(a); break;
-    case kKBcgK4: bcg_k4<double><<<P.g_vec, kBlock, 0, s>>>(a); break;
+    case kKBcgK3: bcg_k3<double><<<P.g_k3, kBlock, 0, s>>>(a); break;
+    case kKBcgK4: bcg_k4<double><<<P.g_k4, kBlock, 0, s>>>(a); break;
     case kKBcgKt: bcg_kt<double><<<P.g_tile, kBlock, 0, s>>>(a); break;
-    case kKBcgKr: bcg_kr<double><<<P.g_vec, kBlock, 0, s>>>(a); break;
+    case kKBcgKr: bcg_kr<double><<<P.g_k4, kBlock, 0, s>>>(a); break;
   }
 }
 
@@ -86,12 +86,14 @@ static gsk_status bcg_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, voi
   if (A->n > 0 && (!b || !x)) return ctx->fail(GSK_ERR_ARG, "NULL b or x");
   const int n = A->n;
   P.wmode = opts.weights ? 2 : (opts.metric == GSK_METRIC_PLAIN ? 1 : 0);
-  P.g_tile = ctx->grid_for((n + 31) / 32, kWarpsPerBlock, 8);
-  // vector kernels: 4 blocks per SM, so that each thread sums many rows
-  // before the (FP64) block reduction
-  P.g_vec = ctx->grid_for((n + 1) / 2, kBlock, 4);
-  const int g_all = ctx->grid_for(n, kBlock, 8);
-  const int gmax = g_all > P.g_tile ? g_all : P.g_tile;
+  P.g_tile = ctx->spmv_grid(n);
+  // vector kernels (two FP64 rows per thread): as many blocks as fit, so
+  // that enough loads are in flight to cover the HBM latency
+  P.g_k2a = ctx->occ_grid((const void*)bcg_k2a<double>, (n + 1) / 2, kBlock);
+  P.g_k3 = ctx->occ_grid((const void*)bcg_k3<double>, (n + 1) / 2, kBlock);
+  P.g_k4 = ctx->occ_grid((const void*)bcg_k4<double>, (n + 1) / 2, kBlock);
+  int gmax = ctx->grid_for(n, kBlock, 8);  // unit check
+  for (int g : {P.g_tile, P.g_k2a, P.g_k3, P.g_k4}) gmax = g > gmax ? g : gmax;
   auto layout = [&](Arena& ar) {
     P.a.err = ar.take<int>(64);
     P.a.cnt = ar.take<unsigned>(64);
@@ -121,6 +123,7 @@ static gsk_status bcg_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, voi
   P.a.w = P.wmode == 0 ? P.wbuf : (P.wmode == 2 ? opts.weights : nullptr);
   P.a.in_graph = 0;
   P.a.h_while = P.a.h_if = 0;
+  P.a.vec_ok = ((uintptr_t)x % 16 == 0) && (P.a.w == nullptr || (uintptr_t)P.a.w % 16 == 0);
   BcgState& hs = P.host_state;
   std::memset(&hs, 0, sizeof(hs));
   hs.tol = tol;

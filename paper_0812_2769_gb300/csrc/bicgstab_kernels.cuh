@@ -27,6 +27,7 @@
 #include <cfloat>
 
 #include "internal.hpp"
+#include "spmv_tma.cuh"
 
 namespace gsk {
 
@@ -51,6 +52,7 @@ struct BcgArgs {
   int* err;
   cudaGraphConditionalHandle h_while, h_if;
   int in_graph;
+  int vec_ok;  // x (and w, if any) are 16-byte aligned: 128-bit loads allowed
 };
 
 template <typename T>
@@ -58,40 +60,34 @@ __device__ __forceinline__ void set_cond(const BcgArgs<T>& a, cudaGraphCondition
   if (a.in_graph) cudaGraphSetConditional(h, v);
 }
 
-#define BCG_TILE_LOOP(a) \
-  for (int tile = blockIdx.x * kWarpsPerBlock + warp_id(), ntiles_ = ((a).n + 31) / 32; tile < ntiles_; \
-       tile += gridDim.x * kWarpsPerBlock)
-
-// Two rows per thread per trip (i and i + stride) so that each thread keeps
-// twice the loads in flight; the row-to-thread map depends only on the grid.
-#define BCG_ROW2_LOOP(a)                                                        \
-  for (int i = blockIdx.x * kBlock + threadIdx.x, stride_ = gridDim.x * kBlock; \
-       i < (a).n; i += 2 * stride_)
+// Vector kernels: each thread takes R = 16/sizeof(T) consecutive rows per
+// trip (128-bit loads of the workspace vectors, which are 256-byte aligned);
+// the last partial group, and everything when the caller's x or weights are
+// not 16-byte aligned, takes the scalar path.  The row-to-thread map depends
+// only on the grid.
+#define BCG_VEC_LOOP(a, R)                                                                         \
+  for (int i0 = (R) * (blockIdx.x * kBlock + threadIdx.x), vstride_ = (R) * gridDim.x * kBlock; \
+       i0 < (a).n; i0 += vstride_)
 
 __device__ __forceinline__ double wgt(const double* w, bool wid, int i) { return wid ? 1.0 : __ldg(w + i); }
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) bcg_init(BcgArgs<T> a) {
-  __shared__ TileStage<T, kStageCap> stage[kWarpsPerBlock];
+  __shared__ PipeSmem<T> pipe;
   __shared__ double blk[2], tot[2];
-  double* sm = reinterpret_cast<double*>(stage);  // reduction scratch after the tile loop
+  double* sm = reinterpret_cast<double*>(&pipe);  // reduction scratch after the product
   BcgState* S = a.S;
   const bool wid = S->w_identity;
   double acc[2] = {0.0, 0.0};
-  BCG_TILE_LOOP(a) {
-    const int i = tile * 32 + lane_id();
-    const T ax = csr_tile_row<T, T, kStageCap>(a.rowptr, a.colidx, a.val, a.x, a.n, a.nnz, tile * 32,
-                                                 stage[warp_id()], a.err);
-    if (i < a.n) {
-      const T r = a.b[i] - ax;
-      a.r[i] = r;
-      a.rh[i] = r;
-      a.p[i] = r;
-      const double wr = wgt(a.w, wid, i) * (double)r;
-      acc[0] = fma(wr, wr, acc[0]);
-      acc[1] = fma((double)r, (double)r, acc[1]);
-    }
-  }
+  spmv_rows_tma(a.rowptr, a.colidx, a.val, a.x, a.n, a.nnz, pipe, a.err, [&](int i, T ax) {
+    const T r = a.b[i] - ax;
+    a.r[i] = r;
+    a.rh[i] = r;
+    a.p[i] = r;
+    const double wr = wgt(a.w, wid, i) * (double)r;
+    acc[0] = fma(wr, wr, acc[0]);
+    acc[1] = fma((double)r, (double)r, acc[1]);
+  });
   block_sum<2, kBlock>(acc, sm, blk);
   if (grid_sum(blk, 2, a.red, tot) && threadIdx.x == 0) {
     const int e = *(volatile int*)a.err;
@@ -130,23 +126,18 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) bcg_k1(BcgArgs<T> a) {
   BcgState* S = a.S;
   if (S->stop) return;
-  __shared__ TileStage<T, kStageCap> stage[kWarpsPerBlock];
+  __shared__ PipeSmem<T> pipe;
   __shared__ double blk[2], tot[2];
-  double* sm = reinterpret_cast<double*>(stage);  // reduction scratch after the tile loop
+  double* sm = reinterpret_cast<double*>(&pipe);  // reduction scratch after the product
   using Acc = typename AccOf<T>::type;
   const T* __restrict__ rh = a.rh;
   T* __restrict__ vout = a.v;
   Acc acc[2] = {Acc(0), Acc(0)};
-  BCG_TILE_LOOP(a) {
-    const int i = tile * 32 + lane_id();
-    const T v = csr_tile_row<T, T, kStageCap>(a.rowptr, a.colidx, a.val, a.p, a.n, a.nnz, tile * 32,
-                                                stage[warp_id()], a.err);
-    if (i < a.n) {
-      vout[i] = v;
-      acc[0] = fma((Acc)rh[i], (Acc)v, acc[0]);
-      acc[1] = fma((Acc)v, (Acc)v, acc[1]);
-    }
-  }
+  spmv_rows_tma(a.rowptr, a.colidx, a.val, a.p, a.n, a.nnz, pipe, a.err, [&](int i, T v) {
+    vout[i] = v;
+    acc[0] = fma((Acc)rh[i], (Acc)v, acc[0]);
+    acc[1] = fma((Acc)v, (Acc)v, acc[1]);
+  });
   const double accd[2] = {(double)acc[0], (double)acc[1]};
   block_sum<2, kBlock>(accd, sm, blk);
   if (grid_sum(blk, 2, a.red, tot) && threadIdx.x == 0) {
@@ -162,6 +153,41 @@ __global__ void __launch_bounds__(kBlock) bcg_k1(BcgArgs<T> a) {
   }
 }
 
+// s = r - alpha v and ||W s||^2, with the weights' presence (WID: W = I) a
+// compile-time choice: a runtime-uniform branch inside the row loop would be
+// if-converted, and the predicated-off FP64 multiply still costs pipe time.
+template <bool WID, typename T, typename Acc>
+__device__ __forceinline__ Acc bcg_k2a_rows(const BcgArgs<T>& a, Acc alpha) {
+  constexpr int R = Vec16<T>::R;
+  const T* __restrict__ r = a.r;
+  const T* __restrict__ v = a.v;
+  T* __restrict__ s = a.s;
+  Acc acc = Acc(0);
+  BCG_VEC_LOOP(a, R) {
+    if (i0 + R <= a.n && (WID || a.vec_ok)) {
+      const Vec16<T> rv = vload(r + i0), vv = vload(v + i0);
+      Vec16<T> sv;
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        sv.v[q] = (T)fma(-alpha, (Acc)vv.v[q], (Acc)rv.v[q]);
+        Acc w1 = (Acc)sv.v[q];
+        if (!WID) w1 *= (Acc)__ldg(a.w + i0 + q);
+        acc = fma(w1, w1, acc);
+      }
+      vstore(s + i0, sv);
+    } else {
+      for (int i = i0; i < min(i0 + R, a.n); ++i) {
+        const T s1 = (T)fma(-alpha, (Acc)v[i], (Acc)r[i]);
+        s[i] = s1;
+        Acc w1 = (Acc)s1;
+        if (!WID) w1 *= (Acc)__ldg(a.w + i);
+        acc = fma(w1, w1, acc);
+      }
+    }
+  }
+  return acc;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock) bcg_k2a(BcgArgs<T> a) {
   BcgState* S = a.S;
@@ -169,30 +195,8 @@ __global__ void __launch_bounds__(kBlock) bcg_k2a(BcgArgs<T> a) {
   __shared__ double sm[1 * kBlock], blk[1], tot[1];
   using Acc = typename AccOf<T>::type;
   const Acc alpha = (Acc)S->alpha;
-  const bool wid = S->w_identity;
-  const T* __restrict__ r = a.r;
-  const T* __restrict__ v = a.v;
-  T* __restrict__ s = a.s;
-  Acc acc[1] = {Acc(0)};
-  BCG_ROW2_LOOP(a) {
-    const int i2 = i + stride_;
-    const bool two = i2 < a.n;
-    const Acc r1 = (Acc)r[i], v1 = (Acc)v[i];
-    const Acc r2 = two ? (Acc)r[i2] : Acc(0), v2 = two ? (Acc)v[i2] : Acc(0);
-    const T s1 = (T)fma(-alpha, v1, r1);
-    s[i] = s1;
-    Acc w1 = (Acc)s1;
-    if (!wid) w1 *= (Acc)__ldg(a.w + i);
-    acc[0] = fma(w1, w1, acc[0]);
-    if (two) {
-      const T s2 = (T)fma(-alpha, v2, r2);
-      s[i2] = s2;
-      Acc w2 = (Acc)s2;
-      if (!wid) w2 *= (Acc)__ldg(a.w + i2);
-      acc[0] = fma(w2, w2, acc[0]);
-    }
-  }
-  const double accd[1] = {(double)acc[0]};
+  const Acc acc = S->w_identity ? bcg_k2a_rows<true>(a, alpha) : bcg_k2a_rows<false>(a, alpha);
+  const double accd[1] = {(double)acc};
   block_sum<1, kBlock>(accd, sm, blk);
   if (grid_sum(blk, 1, a.red, tot) && threadIdx.x == 0) {
     const double mus = sqrt(tot[0]) / S->mu0;
@@ -205,23 +209,18 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) bcg_k2b(BcgArgs<T> a) {
   BcgState* S = a.S;
   if (S->stop || S->halfexit) return;
-  __shared__ TileStage<T, kStageCap> stage[kWarpsPerBlock];
+  __shared__ PipeSmem<T> pipe;
   __shared__ double blk[2], tot[2];
-  double* sm = reinterpret_cast<double*>(stage);  // reduction scratch after the tile loop
+  double* sm = reinterpret_cast<double*>(&pipe);  // reduction scratch after the product
   using Acc = typename AccOf<T>::type;
   const T* __restrict__ sv = a.s;
   T* __restrict__ tout = a.t;
   Acc acc[2] = {Acc(0), Acc(0)};
-  BCG_TILE_LOOP(a) {
-    const int i = tile * 32 + lane_id();
-    const T t = csr_tile_row<T, T, kStageCap>(a.rowptr, a.colidx, a.val, a.s, a.n, a.nnz, tile * 32,
-                                                stage[warp_id()], a.err);
-    if (i < a.n) {
-      tout[i] = t;
-      acc[0] = fma((Acc)t, (Acc)sv[i], acc[0]);
-      acc[1] = fma((Acc)t, (Acc)t, acc[1]);
-    }
-  }
+  spmv_rows_tma(a.rowptr, a.colidx, a.val, a.s, a.n, a.nnz, pipe, a.err, [&](int i, T t) {
+    tout[i] = t;
+    acc[0] = fma((Acc)t, (Acc)sv[i], acc[0]);
+    acc[1] = fma((Acc)t, (Acc)t, acc[1]);
+  });
   const double accd[2] = {(double)acc[0], (double)acc[1]};
   block_sum<2, kBlock>(accd, sm, blk);
   if (grid_sum(blk, 2, a.red, tot) && threadIdx.x == 0) {
@@ -236,9 +235,8 @@ __global__ void __launch_bounds__(kBlock) bcg_k2b(BcgArgs<T> a) {
   }
 }
 
-template <typename T, typename Acc>
-__device__ __forceinline__ void bcg_k3_row(const BcgArgs<T>& a, int i, Acc alpha, Acc omega, bool wid,
-                                           Acc (&acc)[3]) {
+template <bool WID, typename T, typename Acc>
+__device__ __forceinline__ void bcg_k3_row(const BcgArgs<T>& a, int i, Acc alpha, Acc omega, Acc (&acc)[3]) {
   const Acc s = (Acc)a.s[i];
   const Acc x = fma(alpha, (Acc)a.p[i], (Acc)a.x[i]);
   a.x[i] = (T)fma(omega, s, x);
@@ -246,12 +244,45 @@ __device__ __forceinline__ void bcg_k3_row(const BcgArgs<T>& a, int i, Acc alpha
   a.r[i] = r;
   const Acc rd = (Acc)r;
   acc[0] = fma((Acc)a.rh[i], rd, acc[0]);
-  if (wid) {
+  if (WID) {
     acc[1] = fma(rd, rd, acc[1]);
   } else {
     const Acc wr = (Acc)__ldg(a.w + i) * rd;
     acc[1] = fma(wr, wr, acc[1]);
     acc[2] = fma(rd, rd, acc[2]);
+  }
+}
+
+// x += alpha p + omega s, r = s - omega t, and the sums (r^, r), ||W r||^2
+// and (weights present) ||r||^2; WID as in bcg_k2a_rows.
+template <bool WID, typename T, typename Acc>
+__device__ __forceinline__ void bcg_k3_rows(const BcgArgs<T>& a, Acc alpha, Acc omega, Acc (&acc)[3]) {
+  constexpr int R = Vec16<T>::R;
+  BCG_VEC_LOOP(a, R) {
+    if (i0 + R <= a.n && a.vec_ok) {
+      const Vec16<T> sv = vload(a.s + i0), pv = vload(a.p + i0), xv = vload(a.x + i0), tv = vload(a.t + i0),
+                     hv = vload(a.rh + i0);
+      Vec16<T> xo, ro;
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const Acc sq = (Acc)sv.v[q];
+        xo.v[q] = (T)fma(omega, sq, fma(alpha, (Acc)pv.v[q], (Acc)xv.v[q]));
+        ro.v[q] = (T)fma(-omega, (Acc)tv.v[q], sq);
+        const Acc rd = (Acc)ro.v[q];
+        acc[0] = fma((Acc)hv.v[q], rd, acc[0]);
+        if (WID) {
+          acc[1] = fma(rd, rd, acc[1]);
+        } else {
+          const Acc wr = (Acc)__ldg(a.w + i0 + q) * rd;
+          acc[1] = fma(wr, wr, acc[1]);
+          acc[2] = fma(rd, rd, acc[2]);
+        }
+      }
+      vstore(a.x + i0, xo);
+      vstore(a.r + i0, ro);
+    } else {
+      for (int i = i0; i < min(i0 + R, a.n); ++i) bcg_k3_row<WID>(a, i, alpha, omega, acc);
+    }
   }
 }
 
@@ -279,10 +310,8 @@ __global__ void __launch_bounds__(kBlock) bcg_k3(BcgArgs<T> a) {
   const Acc omega = (Acc)S->omega;
   const bool wid = S->w_identity;
   Acc acc[3] = {Acc(0), Acc(0), Acc(0)};
-  BCG_ROW2_LOOP(a) {
-    bcg_k3_row(a, i, alpha, omega, wid, acc);
-    if (i + stride_ < a.n) bcg_k3_row(a, i + stride_, alpha, omega, wid, acc);
-  }
+  if (wid) bcg_k3_rows<true>(a, alpha, omega, acc);
+  else bcg_k3_rows<false>(a, alpha, omega, acc);
   const double accd[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
   block_sum<3, kBlock>(accd, sm, blk);
   if (grid_sum(blk, 3, a.red, tot) && threadIdx.x == 0) {
@@ -324,13 +353,18 @@ __global__ void __launch_bounds__(kBlock) bcg_k4(BcgArgs<T> a) {
   const T* __restrict__ r = a.r;
   const T* __restrict__ v = a.v;
   T* __restrict__ p = a.p;
-  BCG_ROW2_LOOP(a) {
-    const int i2 = i + stride_;
-    const bool two = i2 < a.n;
-    const Acc p1 = (Acc)p[i], v1 = (Acc)v[i], r1 = (Acc)r[i];
-    const Acc p2 = two ? (Acc)p[i2] : Acc(0), v2 = two ? (Acc)v[i2] : Acc(0), r2 = two ? (Acc)r[i2] : Acc(0);
-    p[i] = (T)fma(beta, fma(-omega, v1, p1), r1);
-    if (two) p[i2] = (T)fma(beta, fma(-omega, v2, p2), r2);
+  constexpr int R = Vec16<T>::R;
+  BCG_VEC_LOOP(a, R) {
+    if (i0 + R <= a.n) {
+      const Vec16<T> pv = vload(p + i0), vv = vload(v + i0), rv = vload(r + i0);
+      Vec16<T> po;
+#pragma unroll
+      for (int q = 0; q < R; ++q)
+        po.v[q] = (T)fma(beta, fma(-omega, (Acc)vv.v[q], (Acc)pv.v[q]), (Acc)rv.v[q]);
+      vstore(p + i0, po);
+    } else {
+      for (int i = i0; i < a.n; ++i) p[i] = (T)fma(beta, fma(-omega, (Acc)v[i], (Acc)p[i]), (Acc)r[i]);
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(a, a.h_while, 1u);
 }
@@ -339,23 +373,18 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) bcg_kt(BcgArgs<T> a) {
   BcgState* S = a.S;
   if (!(S->check || S->stop)) return;  // the graph's IF node already excludes this
-  __shared__ TileStage<T, kStageCap> stage[kWarpsPerBlock];
+  __shared__ PipeSmem<T> pipe;
   __shared__ double blk[2], tot[2];
-  double* sm = reinterpret_cast<double*>(stage);  // reduction scratch after the tile loop
+  double* sm = reinterpret_cast<double*>(&pipe);  // reduction scratch after the product
   const bool wid = S->w_identity;
   double acc[2] = {0.0, 0.0};
-  BCG_TILE_LOOP(a) {
-    const int i = tile * 32 + lane_id();
-    const T ax = csr_tile_row<T, T, kStageCap>(a.rowptr, a.colidx, a.val, a.x, a.n, a.nnz, tile * 32,
-                                                 stage[warp_id()], a.err);
-    if (i < a.n) {
-      const T t = a.b[i] - ax;
-      a.t[i] = t;
-      const double wt = wgt(a.w, wid, i) * (double)t;
-      acc[0] = fma(wt, wt, acc[0]);
-      acc[1] = fma((double)t, (double)t, acc[1]);
-    }
-  }
+  spmv_rows_tma(a.rowptr, a.colidx, a.val, a.x, a.n, a.nnz, pipe, a.err, [&](int i, T ax) {
+    const T t = a.b[i] - ax;
+    a.t[i] = t;
+    const double wt = wgt(a.w, wid, i) * (double)t;
+    acc[0] = fma(wt, wt, acc[0]);
+    acc[1] = fma((double)t, (double)t, acc[1]);
+  });
   block_sum<2, kBlock>(acc, sm, blk);
   if (grid_sum(blk, 2, a.red, tot) && threadIdx.x == 0) {
     S->mu_true = sqrt(tot[0]) / S->mu0;

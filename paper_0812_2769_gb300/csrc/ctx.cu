@@ -1,5 +1,6 @@
 // Context management and the thin C ABI entry points that are not solvers.
 #include <cmath>
+#include <cstdlib>
 
 #include "internal.hpp"
 
@@ -66,6 +67,10 @@ gsk_status gsk_ctx_create(gsk_ctx** out, int device) {
   ctx->device = device;
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (const char* v = std::getenv("GSK_SPMV_BLOCKS_PER_SM")) {
+    const int k = std::atoi(v);
+    if (k >= 1 && k <= 5) ctx->spmv_per_sm = k;
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);

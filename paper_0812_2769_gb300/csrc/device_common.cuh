@@ -23,7 +23,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kGroup = 16;  // blocks per first-level reduction group
 
 // error bits written by kernels into a device status word
-enum : int { kErrIndex = 1, kErrZeroRow = 2, kErrNonFinite = 4 };
+enum : int { kErrIndex = 1, kErrZeroRow = 2, kErrNonFinite = 4, kErrTimeout = 8 };
 
 // Scratch for one grid-wide reduction site.
 struct GridRed {
@@ -44,6 +44,23 @@ template <>
 struct AccOf<float> {
   using type = float;
 };
+
+// 16-byte vectors of consecutive entries (2 doubles or 4 floats) for
+// 128-bit loads and stores on 16-byte aligned addresses.
+template <typename T>
+struct Vec16 {
+  static constexpr int R = 16 / sizeof(T);
+  T v[R];
+} __attribute__((aligned(16)));
+
+template <typename T>
+__device__ __forceinline__ Vec16<T> vload(const T* p) {
+  return *reinterpret_cast<const Vec16<T>*>(p);
+}
+template <typename T>
+__device__ __forceinline__ void vstore(T* p, const Vec16<T>& x) {
+  *reinterpret_cast<Vec16<T>*>(p) = x;
+}
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }

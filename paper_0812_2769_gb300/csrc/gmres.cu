@@ -8,7 +8,7 @@ namespace gsk {
 // ------------------------------------------------------------------ host
 
 struct GmPlan {
-  int g_tile, g_vec, wmode, KP;
+  int g_tile, g_gd, g_gb, g_gc, g_gx, wmode, KP;
   GmArgs<double> a;
   double* wbuf;
   GmState host_state;
@@ -22,13 +22,23 @@ static void gm_launch_kp(gsk_ctx* ctx, GmPlan& P, int k, cudaStream_t s) {
     case kKUnitCheck: launch_unit_check(ctx, a.n, P.wbuf, a.red, &a.S->w_identity, s); break;
     case kKGmInit: gm_residual<double, true><<<P.g_tile, kBlock, 0, s>>>(a); break;
     case kKGmGa: gm_ga<double><<<P.g_tile, kBlock, 0, s>>>(a); break;
-    case kKGmGd: gm_gd<double, KP><<<P.g_vec, kBlock, 0, s>>>(a); break;
-    case kKGmGb: gm_gb<double, KP><<<P.g_vec, kBlock, 0, s>>>(a); break;
-    case kKGmGc: gm_gc<double, KP><<<P.g_vec, kBlock, 0, s>>>(a); break;
+    case kKGmGd: gm_gd<double, KP><<<P.g_gd, kBlock, 0, s>>>(a); break;
+    case kKGmGb: gm_gb<double, KP><<<P.g_gb, kBlock, 0, s>>>(a); break;
+    case kKGmGc: gm_gc<double, KP><<<P.g_gc, kBlock, 0, s>>>(a); break;
     case kKGmGy: gm_gy<double><<<1, 32, 0, s>>>(a); break;
-    case kKGmGx: gm_gx<double, KP><<<P.g_vec, kBlock, 0, s>>>(a); break;
+    case kKGmGx: gm_gx<double, KP><<<P.g_gx, kBlock, 0, s>>>(a); break;
     case kKGmGr: gm_residual<double, false><<<P.g_tile, kBlock, 0, s>>>(a); break;
   }
+}
+
+// Grids of the basis kernels (CGS passes: two FP64 rows per thread; x
+// update: one): as many blocks as fit at each kernel's occupancy.
+template <int KP>
+static void gm_grids_kp(gsk_ctx* ctx, GmPlan& P, int n) {
+  P.g_gd = ctx->occ_grid((const void*)gm_gd<double, KP>, (n + 1) / 2, kBlock);
+  P.g_gb = ctx->occ_grid((const void*)gm_gb<double, KP>, (n + 1) / 2, kBlock);
+  P.g_gc = ctx->occ_grid((const void*)gm_gc<double, KP>, (n + 1) / 2, kBlock);
+  P.g_gx = ctx->occ_grid((const void*)gm_gx<double, KP>, n, kBlock);
 }
 
 static void gm_launch(gsk_ctx* ctx, GmPlan& P, int k, cudaStream_t s) {
@@ -92,9 +102,12 @@ static gsk_status gm_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, void
   P.wmode = opts.weights ? 2 : (opts.metric == GSK_METRIC_PLAIN ? 1 : 0);
   P.KP = m <= 16 ? 16 : (m <= 32 ? 32 : 64);
   // tile (SpMV) kernels carry no per-column accumulators: full occupancy
-  P.g_tile = ctx->grid_for((n + 31) / 32, kWarpsPerBlock, 8);
-  P.g_vec = ctx->grid_for(n, kBlock, P.KP <= 16 ? 4 : 2);
-  const int gmax = P.g_tile > P.g_vec ? P.g_tile : P.g_vec;
+  P.g_tile = ctx->spmv_grid(n);
+  if (P.KP == 16) gm_grids_kp<16>(ctx, P, n);
+  else if (P.KP == 32) gm_grids_kp<32>(ctx, P, n);
+  else gm_grids_kp<64>(ctx, P, n);
+  int gmax = ctx->grid_for(n, kBlock, 8);  // unit check
+  for (int g : {P.g_tile, P.g_gd, P.g_gb, P.g_gc}) gmax = g > gmax ? g : gmax;
   const long long ldv = ((long long)n + 63) / 64 * 64;
   GmArgs<double>& a = P.a;
   std::memset(&a, 0, sizeof(a));

@@ -23,7 +23,8 @@
 //
 // Stopping (Sec. 2.2): a cycle ends when |g_{j+1}| < tau * ||r0|| (the
 // least-squares residual relative to the initial residual), at numerical
-// breakdown h_{j+1,j} <= hbrk ||A v_j|| (hbrk = 1e-14 in FP64), after m
+// breakdown h_{j+1,j} <= hbrk ||A v_j|| (hbrk = 1e-14 in FP64; ||A v_j|| from
+// the CGS coefficients and h_{j+1,j}, equal to the direct norm up to rounding), after m
 // steps, or at maxit.  The
 // true metric ||W(b - Ax)|| / ||W(b - Ax0)|| (W = GS(2) scales of A) decides
 // convergence; if the estimate met tau but the metric did not, tau is
@@ -33,6 +34,7 @@
 #include <cfloat>
 
 #include "internal.hpp"
+#include "spmv_tma.cuh"
 
 namespace gsk {
 
@@ -66,9 +68,6 @@ __device__ __forceinline__ void gm_set_cond(const GmArgs<T>& a, cudaGraphConditi
   if (a.in_graph) cudaGraphSetConditional(h, v);
 }
 
-#define GM_TILE_LOOP(a) \
-  for (int tile = blockIdx.x * kWarpsPerBlock + warp_id(), ntiles_ = ((a).n + 31) / 32; tile < ntiles_; \
-       tile += gridDim.x * kWarpsPerBlock)
 #define GM_ROW_LOOP(a) for (int i = blockIdx.x * kBlock + threadIdx.x; i < (a).n; i += gridDim.x * kBlock)
 
 __device__ __forceinline__ double gm_wgt(const double* w, bool wid, int i) { return wid ? 1.0 : __ldg(w + i); }
@@ -91,7 +90,7 @@ __device__ __forceinline__ void block_sum_chunked(const A (&v)[NV], int nv, doub
 
 template <typename T>
 union GmSmem {
-  TileStage<T, kStageCap> stage[kWarpsPerBlock];
+  PipeSmem<T> pipe;
   double table[16 * kBlock];
 };
 
@@ -103,18 +102,13 @@ __global__ void __launch_bounds__(kBlock) gm_residual(GmArgs<T> a) {
   GmState* S = a.S;
   const bool wid = S->w_identity;
   double acc[2] = {0.0, 0.0};
-  GM_TILE_LOOP(a) {
-    const int i = tile * 32 + lane_id();
-    const T ax = csr_tile_row<T, T, kStageCap>(a.rowptr, a.colidx, a.val, a.x, a.n, a.nnz, tile * 32,
-                                                 sm.stage[warp_id()], a.err);
-    if (i < a.n) {
-      const T r = a.b[i] - ax;
-      a.V[i] = r;
-      const double wr = gm_wgt(a.w, wid, i) * (double)r;
-      acc[0] = fma(wr, wr, acc[0]);
-      acc[1] = fma((double)r, (double)r, acc[1]);
-    }
-  }
+  spmv_rows_tma(a.rowptr, a.colidx, a.val, a.x, a.n, a.nnz, sm.pipe, a.err, [&](int i, T ax) {
+    const T r = a.b[i] - ax;
+    a.V[i] = r;
+    const double wr = gm_wgt(a.w, wid, i) * (double)r;
+    acc[0] = fma(wr, wr, acc[0]);
+    acc[1] = fma((double)r, (double)r, acc[1]);
+  });
   block_sum_chunked<2>(acc, 2, sm.table, blk);
   if (grid_sum(blk, 2, a.red, tot) && threadIdx.x == 0) {
     const int e = *(volatile int*)a.err;
@@ -174,53 +168,92 @@ __global__ void __launch_bounds__(kBlock) gm_residual(GmArgs<T> a) {
   }
 }
 
-// Arnoldi step, product: w = A v_j stored in V[:, j+1]; ||w||^2 (the
-// reference for the breakdown test).
+// Arnoldi step, product: w = A v_j stored in V[:, j+1].  No reduction here:
+// the breakdown reference ||A v_j|| follows from the CGS coefficients and
+// the final norm (Pythagoras over the orthonormal basis), taken in gm_gc.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) gm_ga(GmArgs<T> a) {
-  __shared__ GmSmem<T> sm;
-  __shared__ double res[1], tot[1];
+  __shared__ PipeSmem<T> pipe;
   const GmState* S = a.S;
   const int j = S->j;
   const T* vj = a.V + (long long)j * a.ldv;
   T* __restrict__ wout = a.V + (long long)(j + 1) * a.ldv;
   using Acc = typename AccOf<T>::type;
   const Acc sj = (Acc)a.sig[j];
-  Acc ww[1] = {Acc(0)};
-  GM_TILE_LOOP(a) {
-    const int i = tile * 32 + lane_id();
-    const T av = csr_tile_row<T, T, kStageCap>(a.rowptr, a.colidx, a.val, vj, a.n, a.nnz, tile * 32,
-                                                 sm.stage[warp_id()], a.err);
-    if (i < a.n) {
-      const T w = (T)(sj * (Acc)av);
-      wout[i] = w;
-      ww[0] = fma((Acc)w, (Acc)w, ww[0]);
+  spmv_rows_tma(a.rowptr, a.colidx, a.val, vj, a.n, a.nnz, pipe, a.err,
+                [&](int i, T av) { wout[i] = (T)(sj * (Acc)av); });
+}
+
+// Row loop of the CGS passes: each thread takes R = 16/sizeof(T) consecutive
+// rows (one 128-bit load per basis column); V's columns are 16-byte aligned
+// (leading dimension a multiple of 64) and only the last partial group of
+// rows takes the scalar path.
+#define GM_VEC_LOOP(a, R)                                                                          \
+  for (int i0 = (R) * (blockIdx.x * kBlock + threadIdx.x), vstride_ = (R) * gridDim.x * kBlock; \
+       i0 < (a).n; i0 += vstride_)
+
+// Calls f(c) for c = 0 .. k-1 in groups of four, c a compile-time constant
+// after unrolling (so per-column accumulators stay in registers).  The
+// ragged last group takes one uniform branch per count: no FP64 instruction
+// is issued for a column c >= k (on this part a predicated-off FP64
+// instruction still costs its pipe time).
+template <int KP, typename F>
+__device__ __forceinline__ void for_columns(int k, F&& f) {
+#pragma unroll
+  for (int c0 = 0; c0 < KP; c0 += 4) {
+    if (c0 + 4 <= k) {
+      f(c0);
+      f(c0 + 1);
+      f(c0 + 2);
+      f(c0 + 3);
+    } else if (c0 < k) {
+      switch (k - c0) {
+        case 3:
+          f(c0);
+          f(c0 + 1);
+          f(c0 + 2);
+          break;
+        case 2:
+          f(c0);
+          f(c0 + 1);
+          break;
+        default:
+          f(c0);
+          break;
+      }
     }
   }
-  block_sum_chunked<1>(ww, 1, sm.table, res);
-  if (grid_sum(res, 1, a.red, tot) && threadIdx.x == 0) a.S->aw_norm = sqrt(tot[0]);
 }
 
 // CGS pass 1: h1 = sig .* (V_k^T w).
 template <typename T, int KP>
 __global__ void __launch_bounds__(kBlock) gm_gd(GmArgs<T> a) {
+  using Acc = typename AccOf<T>::type;
+  constexpr int R = Vec16<T>::R;
   __shared__ double table[16 * kBlock], res[KP], tot[KP];
   const GmState* S = a.S;
   const int j = S->j, k = j + 1;
-  using Acc = typename AccOf<T>::type;
   const T* __restrict__ wv = a.V + (long long)(j + 1) * a.ldv;
   Acc acc[KP];
 #pragma unroll
   for (int c = 0; c < KP; ++c) acc[c] = Acc(0);
-  GM_ROW_LOOP(a) {
-    const Acc w = (Acc)wv[i];
+  GM_VEC_LOOP(a, R) {
+    if (i0 + R <= a.n) {
+      const Vec16<T> w = vload(wv + i0);
+      for_columns<KP>(k, [&](int c) {
+        const Vec16<T> v = vload(a.V + (long long)c * a.ldv + i0);
 #pragma unroll
-    for (int c0 = 0; c0 < KP; c0 += 4)
-      if (c0 < k) {
+        for (int r = 0; r < R; ++r) acc[c] = fma((Acc)v.v[r], (Acc)w.v[r], acc[c]);
+      });
+    } else {
+      for (int i = i0; i < a.n; ++i) {
+        const Acc w = (Acc)wv[i];
+        for (int c = 0; c < k; ++c)
 #pragma unroll
-        for (int c = c0; c < c0 + 4; ++c)
-          if (c < k) acc[c] = fma((Acc)a.V[(long long)c * a.ldv + i], w, acc[c]);
+          for (int q = 0; q < KP; ++q)
+            if (q == c) acc[q] = fma((Acc)a.V[(long long)c * a.ldv + i], w, acc[q]);
       }
+    }
   }
   block_sum_chunked<KP>(acc, k, table, res);
   if (grid_sum(res, k, a.red, tot)) {
@@ -232,6 +265,7 @@ __global__ void __launch_bounds__(kBlock) gm_gd(GmArgs<T> a) {
 template <typename T, int KP>
 __global__ void __launch_bounds__(kBlock) gm_gb(GmArgs<T> a) {
   using Acc = typename AccOf<T>::type;
+  constexpr int R = Vec16<T>::R;
   __shared__ Acc coef[KP];
   __shared__ double table[16 * kBlock], res[KP], tot[KP];
   const GmState* S = a.S;
@@ -242,24 +276,38 @@ __global__ void __launch_bounds__(kBlock) gm_gb(GmArgs<T> a) {
   Acc acc[KP];
 #pragma unroll
   for (int c = 0; c < KP; ++c) acc[c] = Acc(0);
-  GM_ROW_LOOP(a) {
-    Acc w = (Acc)wv[i];
+  GM_VEC_LOOP(a, R) {
+    if (i0 + R <= a.n) {
+      const Vec16<T> w0 = vload(wv + i0);
+      Acc w[R];
 #pragma unroll
-    for (int c0 = 0; c0 < KP; c0 += 4)
-      if (c0 < k) {
+      for (int r = 0; r < R; ++r) w[r] = (Acc)w0.v[r];
+      for_columns<KP>(k, [&](int c) {
+        const Vec16<T> v = vload(a.V + (long long)c * a.ldv + i0);
 #pragma unroll
-        for (int c = c0; c < c0 + 4; ++c)
-          if (c < k) w = fma(-(Acc)a.V[(long long)c * a.ldv + i], coef[c], w);
+        for (int r = 0; r < R; ++r) w[r] = fma(-(Acc)v.v[r], coef[c], w[r]);
+      });
+      Vec16<T> wt;
+#pragma unroll
+      for (int r = 0; r < R; ++r) wt.v[r] = (T)w[r];
+      vstore(wv + i0, wt);
+      for_columns<KP>(k, [&](int c) {
+        const Vec16<T> v = vload(a.V + (long long)c * a.ldv + i0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[c] = fma((Acc)v.v[r], (Acc)wt.v[r], acc[c]);
+      });
+    } else {
+      for (int i = i0; i < a.n; ++i) {
+        Acc w = (Acc)wv[i];
+        for (int c = 0; c < k; ++c) w = fma(-(Acc)a.V[(long long)c * a.ldv + i], coef[c], w);
+        const T wt = (T)w;
+        wv[i] = wt;
+        for (int c = 0; c < k; ++c)
+#pragma unroll
+          for (int q = 0; q < KP; ++q)
+            if (q == c) acc[q] = fma((Acc)a.V[(long long)c * a.ldv + i], (Acc)wt, acc[q]);
       }
-    const T wt = (T)w;
-    wv[i] = wt;
-#pragma unroll
-    for (int c0 = 0; c0 < KP; c0 += 4)
-      if (c0 < k) {
-#pragma unroll
-        for (int c = c0; c < c0 + 4; ++c)
-          if (c < k) acc[c] = fma((Acc)a.V[(long long)c * a.ldv + i], (Acc)wt, acc[c]);
-      }
+    }
   }
   block_sum_chunked<KP>(acc, k, table, res);
   if (grid_sum(res, k, a.red, tot)) {
@@ -273,32 +321,54 @@ template <typename T, int KP>
 __global__ void __launch_bounds__(kBlock) gm_gc(GmArgs<T> a) {
   using Acc = typename AccOf<T>::type;
   __shared__ Acc coef[KP];
-  __shared__ double table[16 * kBlock], res[1], tot[1];
+  __shared__ double table[kBlock], res[1], tot[1];
   GmState* S = a.S;
   const int j = S->j, k = j + 1;
   T* wv = a.V + (long long)(j + 1) * a.ldv;
   for (int c = threadIdx.x; c < k; c += kBlock) coef[c] = (Acc)(a.sig[c] * a.h2[c]);
   __syncthreads();
+  constexpr int R = Vec16<T>::R;
   Acc acc[1] = {Acc(0)};
-  GM_ROW_LOOP(a) {
-    Acc w = (Acc)wv[i];
+  GM_VEC_LOOP(a, R) {
+    if (i0 + R <= a.n) {
+      const Vec16<T> w0 = vload(wv + i0);
+      Acc w[R];
 #pragma unroll
-    for (int c0 = 0; c0 < KP; c0 += 4)
-      if (c0 < k) {
+      for (int r = 0; r < R; ++r) w[r] = (Acc)w0.v[r];
+      for_columns<KP>(k, [&](int c) {
+        const Vec16<T> v = vload(a.V + (long long)c * a.ldv + i0);
 #pragma unroll
-        for (int c = c0; c < c0 + 4; ++c)
-          if (c < k) w = fma(-(Acc)a.V[(long long)c * a.ldv + i], coef[c], w);
+        for (int r = 0; r < R; ++r) w[r] = fma(-(Acc)v.v[r], coef[c], w[r]);
+      });
+      Vec16<T> wt;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        wt.v[r] = (T)w[r];
+        acc[0] = fma((Acc)wt.v[r], (Acc)wt.v[r], acc[0]);
       }
-    const T wt = (T)w;
-    wv[i] = wt;
-    acc[0] = fma((Acc)wt, (Acc)wt, acc[0]);
+      vstore(wv + i0, wt);
+    } else {
+      for (int i = i0; i < a.n; ++i) {
+        Acc w = (Acc)wv[i];
+        for (int c = 0; c < k; ++c) w = fma(-(Acc)a.V[(long long)c * a.ldv + i], coef[c], w);
+        const T wt = (T)w;
+        wv[i] = wt;
+        acc[0] = fma((Acc)wt, (Acc)wt, acc[0]);
+      }
+    }
   }
-  block_sum_chunked<1>(acc, 1, table, res);
+  const double accd[1] = {(double)acc[0]};
+  block_sum<1, kBlock>(accd, table, res);
   if (grid_sum(res, 1, a.red, tot) && threadIdx.x == 0) {
     const int ld = a.m + 1;
     double* hcol = a.H + (long long)j * ld;
     for (int c = 0; c <= j; ++c) hcol[c] = a.h1[c] + a.h2[c];
     const double hnext = sqrt(tot[0]);
+    // ||A v_j||^2 = ||h1 + h2||^2 + hnext^2 (w's parts along the orthonormal
+    // basis and orthogonal to it)
+    double aw2 = hnext * hnext;
+    for (int c = 0; c <= j; ++c) aw2 = fma(hcol[c], hcol[c], aw2);
+    S->aw_norm = sqrt(aw2);
     S->iters += 1;
     for (int q = 0; q < j; ++q) {
       const double t0 = a.cs[q] * hcol[q] + a.sn[q] * hcol[q + 1];
@@ -364,13 +434,7 @@ __global__ void __launch_bounds__(kBlock) gm_gx(GmArgs<T> a) {
   __syncthreads();
   GM_ROW_LOOP(a) {
     double x = (double)a.x[i];
-#pragma unroll
-    for (int c0 = 0; c0 < KP; c0 += 4)
-      if (c0 < k) {
-#pragma unroll
-        for (int c = c0; c < c0 + 4; ++c)
-          if (c < k) x = fma((double)a.V[(long long)c * a.ldv + i], coef[c], x);
-      }
+    for_columns<KP>(k, [&](int c) { x = fma((double)a.V[(long long)c * a.ldv + i], coef[c], x); });
     a.x[i] = (T)x;
   }
 }

@@ -10,6 +10,7 @@
 #include <mutex>
 
 #include "internal.hpp"
+#include "spmv_tma.cuh"
 
 namespace gsk {
 
@@ -99,13 +100,8 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) spmv_kernel(int n, int nnz, const int* __restrict__ rowptr,
                                                       const int* __restrict__ colidx, const T* __restrict__ val,
                                                       const T* __restrict__ x, T* __restrict__ y, int* err) {
-  __shared__ TileStage<T, kStageCap> stage[kWarpsPerBlock];
-  const int ntiles = (n + 31) / 32;
-  for (int tile = blockIdx.x * kWarpsPerBlock + warp_id(); tile < ntiles; tile += gridDim.x * kWarpsPerBlock) {
-    const int r0 = tile * 32;
-    const T v = csr_tile_row<T, T, kStageCap>(rowptr, colidx, val, x, n, nnz, r0, stage[warp_id()], err);
-    if (r0 + lane_id() < n) y[r0 + lane_id()] = v;
-  }
+  __shared__ PipeSmem<T> pipe;
+  spmv_rows_tma(rowptr, colidx, val, x, n, nnz, pipe, err, [&](int i, T v) { y[i] = v; });
 }
 
 // Counts entries of w outside [1 - 4 eps, 1 + 4 eps] (integer compares on
@@ -141,7 +137,7 @@ void launch_unit_check(gsk_ctx* ctx, int n, const double* w, const GridRed& red,
 
 gsk_status launch_spmv(gsk_ctx* ctx, const gsk_csr* A, const void* x, void* y, int* err, cudaStream_t st) {
   if (A->n == 0) return GSK_OK;
-  const int grid = ctx->grid_for((A->n + 31) / 32, kWarpsPerBlock, 8);
+  const int grid = ctx->spmv_grid(A->n);
   if (A->dtype == GSK_F64)
     spmv_kernel<double><<<grid, kBlock, 0, st>>>(A->n, A->nnz, A->rowptr, A->colidx, (const double*)A->val,
                                                   (const double*)x, (double*)y, err);

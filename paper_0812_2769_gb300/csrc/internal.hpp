@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "gsk.h"
@@ -45,6 +46,8 @@ struct Arena {
 struct gsk_ctx {
   int device = 0;
   int num_sms = 0;
+  // blocks per SM of the SpMV-family kernels (GSK_SPMV_BLOCKS_PER_SM, 1..5)
+  int spmv_per_sm = 5;
   std::string last_error;
   // device workspace
   void* ws = nullptr;
@@ -70,6 +73,28 @@ struct gsk_ctx {
   void clear_graphs();
   gsk::GraphEntry* find_graph(const std::vector<uint64_t>& key);
   gsk::GraphEntry* add_graph(const std::vector<uint64_t>& key, cudaGraphExec_t exec);
+  // Grid of the SpMV-family kernels: one 256-row chunk per block trip, at
+  // most spmv_per_sm blocks per SM (each holds a 45 KB shared-memory ring).
+  int spmv_grid(int n) const { return grid_for(((long long)n + 255) / 256, 1, spmv_per_sm); }
+  // Grid of a grid-stride kernel: every block that fits on the device at once
+  // (the kernel's occupancy at kBlock threads, cached per kernel), fewer when
+  // there is less work.
+  std::unordered_map<const void*, int> occ_cache;
+  int occ_grid(const void* kernel, long long work_items, int per_block) {
+    auto it = occ_cache.find(kernel);
+    int per_sm;
+    if (it != occ_cache.end()) {
+      per_sm = it->second;
+    } else {
+      per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+      }
+      occ_cache[kernel] = per_sm;
+    }
+    return grid_for(work_items, per_block, per_sm);
+  }
   int grid_for(long long work_items, int per_block, int per_sm = 8) const {
     long long g = (work_items + per_block - 1) / per_block;
     long long cap = (long long)num_sms * per_sm;
@@ -110,6 +135,7 @@ inline gsk_status check_csr(gsk_ctx* ctx, const gsk_csr* A) {
 
 // Status of the input checks done by the kernels (bits of kErr*).
 inline gsk_status err_bits_status(gsk_ctx* ctx, int bits) {
+  if (bits & kErrTimeout) return ctx->fail(GSK_ERR_TIMEOUT, "a bounded wait for a TMA copy gave up");
   if (bits & kErrIndex) return ctx->fail(GSK_ERR_ARG, "malformed CSR structure (rowptr extent or column index out of range)");
   if (bits & kErrNonFinite) return ctx->fail(GSK_ERR_NONFINITE, "NaN or Inf in the matrix or right-hand side");
   if (bits & kErrZeroRow) return ctx->fail(GSK_ERR_ZERO_ROW, "a row of the matrix is all zeros");

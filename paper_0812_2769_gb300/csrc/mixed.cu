@@ -84,26 +84,20 @@ __global__ void __launch_bounds__(kBlock) mx_convert(MxArgs a) {
 // r = b - A x (FP64); metric and scaling norms; start, continue or stop.
 template <bool INIT>
 __global__ void __launch_bounds__(kBlock) mx_residual(MxArgs a) {
-  __shared__ TileStage<double, kStageCap> stage[kWarpsPerBlock];
+  __shared__ PipeSmem<double> pipe;
   __shared__ double blk[2], tot[2];
-  double* sm = reinterpret_cast<double*>(stage);
+  double* sm = reinterpret_cast<double*>(&pipe);  // reduction scratch after the product
   MxState* S = a.S;
   const bool wid = S->w_identity;
   double acc[2] = {0.0, 0.0};
-  for (int tile = blockIdx.x * kWarpsPerBlock + warp_id(), nt = (a.n + 31) / 32; tile < nt;
-       tile += gridDim.x * kWarpsPerBlock) {
-    const int i = tile * 32 + lane_id();
-    const double ax = csr_tile_row<double, double, kStageCap>(a.rowptr, a.colidx, a.val, a.x, a.n, a.nnz,
-                                                               tile * 32, stage[warp_id()], a.err);
-    if (i < a.n) {
-      const double r = a.b[i] - ax;
-      a.r[i] = r;
-      const double wr = (wid ? 1.0 : __ldg(a.wm + i)) * r;
-      const double w2r = __ldg(a.w2 + i) * r;
-      acc[0] = fma(wr, wr, acc[0]);
-      acc[1] = fma(w2r, w2r, acc[1]);
-    }
-  }
+  spmv_rows_tma(a.rowptr, a.colidx, a.val, a.x, a.n, a.nnz, pipe, a.err, [&](int i, double ax) {
+    const double r = a.b[i] - ax;
+    a.r[i] = r;
+    const double wr = (wid ? 1.0 : __ldg(a.wm + i)) * r;
+    const double w2r = __ldg(a.w2 + i) * r;
+    acc[0] = fma(wr, wr, acc[0]);
+    acc[1] = fma(w2r, w2r, acc[1]);
+  });
   block_sum<2, kBlock>(acc, sm, blk);
   if (grid_sum(blk, 2, a.red, tot) && threadIdx.x == 0) {
     const int e = *(volatile int*)a.err;
@@ -289,9 +283,9 @@ static gsk_status mx_prepare(gsk_ctx* ctx, int solver, const gsk_csr* A, const v
   P.m = solver == 0 ? m : 1;
   P.wmode = opts.weights ? 2 : (opts.metric == GSK_METRIC_PLAIN ? 1 : 0);
   P.KP = m <= 16 ? 16 : (m <= 32 ? 32 : 64);
-  P.g_tile = ctx->grid_for((n + 31) / 32, kWarpsPerBlock, 8);
+  P.g_tile = ctx->spmv_grid(n);
   P.g_vec = ctx->grid_for(n, kBlock, 4);
-  P.g_vec2 = ctx->grid_for((n + 1) / 2, kBlock, 4);
+  P.g_vec2 = ctx->occ_grid((const void*)bcg_k3<float>, (n + 3) / 4, kBlock);  // four FP32 rows per thread
   const int g_gm = ctx->grid_for(n, kBlock, P.KP <= 16 ? 4 : 2);
   int gmax = P.g_tile;
   for (int g : {P.g_vec, P.g_vec2, g_gm, ctx->grid_for(n, kBlock, 8)}) gmax = g > gmax ? g : gmax;
@@ -382,6 +376,7 @@ static gsk_status mx_prepare(gsk_ctx* ctx, int solver, const gsk_csr* A, const v
     bi.cnt = a.cnt;
     bi.err = a.err;
     bi.in_graph = 1;
+    bi.vec_ok = 1;  // every FP32 vector is workspace (256-byte aligned)
     std::memset(&P.hb, 0, sizeof(P.hb));
     P.hb.tol = opts.inner_tol;
     // FP32 rounding noise swamps |<rh, v>| below about FLT_EPSILON ||rh|| ||v||:

@@ -39,7 +39,8 @@ def test_results_same_alone_and_in_the_mix():
                                                                             q.tol, q.precision, 0.0)],
                                                              realtime=False)[0]
         r = mixed[q.rid]
-        assert r.status == alone.status == 0
+        assert r.status == alone.status == 0, (q.rid, q.solver, r.lane, r.status, alone.status,
+                                                [c.last_error() for c in be.ctxs + [be.bctx]])
         assert np.all(np.isfinite(r.x)), q.rid
         assert np.array_equal(r.x, alone.x), q.rid
     summary = serve.summarize(mixed)
