@@ -72,29 +72,6 @@ __device__ __forceinline__ T warp_allsum(T v) {
   return v;
 }
 
-// Sum of cnt entries src[k*stride + q] (q < cnt) for each k < nv, computed by
-// one full warp in a fixed order; the totals are returned in out[k] (written
-// by lane 0 when nv is small, by lane k % 32 otherwise).
-template <int NVMAX>
-__device__ __forceinline__ void warp_sum_table(const double* src, int stride, int cnt, int nv,
-                                               double* out, bool cached) {
-  const int lane = lane_id();
-  if (nv >= 8) {
-    for (int k = lane; k < nv; k += 32) {
-      double s = 0.0;
-      for (int q = 0; q < cnt; ++q) s += cached ? src[k * stride + q] : __ldcg(src + k * stride + q);
-      out[k] = s;
-    }
-  } else {
-    for (int k = 0; k < nv; ++k) {
-      double s = 0.0;
-      for (int q = lane; q < cnt; q += 32) s += cached ? src[k * stride + q] : __ldcg(src + k * stride + q);
-      s = warp_allsum(s);
-      if (lane == 0) out[k] = s;
-    }
-  }
-}
-
 // Block-wide sum of nv per-thread values held in shared memory as
 // tab[k * BLOCK + t] (the table is consumed).  Result in res[k] (shared),
 // valid after the call.  Tree as in block_sum.
@@ -149,12 +126,16 @@ __device__ __forceinline__ void block_sum(const double (&v)[NV], double* sm, dou
 // in every thread).  Returns true in every thread of the one block that
 // finishes last; that block then finds the totals in tot[k] (shared).  The
 // counters are reset so the site can be reused by the next launch.
+// The closing blocks spread the sums over all their warps (one warp per
+// value, lanes over the partials, a fixed shuffle tree), so the serial tail
+// of a launch is a few memory round trips, whatever nv is.
 __device__ __forceinline__ bool grid_sum(const double* blk, int nv, const GridRed& R, double* tot) {
   __shared__ int s_last;
   const int G = gridDim.x, b = blockIdx.x;
   const int g = b / kGroup;
   const int ng = (G + kGroup - 1) / kGroup;
   const int gsize = min(kGroup, G - g * kGroup);
+  const int nwarps = blockDim.x >> 5;
   if (threadIdx.x == 0) {
     for (int k = 0; k < nv; ++k) R.partials[k * G + b] = blk[k];
     __threadfence();
@@ -164,39 +145,34 @@ __device__ __forceinline__ bool grid_sum(const double* blk, int nv, const GridRe
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-  if (warp_id() == 0) {
-    // this block closes group g: sum its gsize partials per value
-    double* gout = R.gpartials;  // [k * ng + g]
-    if (nv >= 8) {
-      for (int k = lane_id(); k < nv; k += 32) {
-        double s = 0.0;
-        for (int q = 0; q < gsize; ++q) s += __ldcg(R.partials + k * G + g * kGroup + q);
-        gout[k * ng + g] = s;
-      }
-    } else {
-      for (int k = 0; k < nv; ++k) {
-        double s = lane_id() < gsize ? __ldcg(R.partials + k * G + g * kGroup + lane_id()) : 0.0;
-        s = warp_allsum(s);
-        if (lane_id() == 0) gout[k * ng + g] = s;
-      }
-    }
-    __syncwarp();
+  // this block closes group g: the sum of its gsize (<= 32) partials per value
+  for (int k = warp_id(); k < nv; k += nwarps) {
+    double v = lane_id() < gsize ? __ldcg(R.partials + k * G + g * kGroup + lane_id()) : 0.0;
+    v = warp_allsum(v);
     if (lane_id() == 0) {
-      R.counters[g] = 0u;
+      R.gpartials[k * ng + g] = v;
       __threadfence();
-      unsigned t = atomicAdd(&R.counters[ng], 1u);
-      s_last = (t == (unsigned)(ng - 1));
     }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R.counters[g] = 0u;
+    __threadfence();
+    unsigned t = atomicAdd(&R.counters[ng], 1u);
+    s_last = (t == (unsigned)(ng - 1));
   }
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-  if (warp_id() == 0) {
-    warp_sum_table<64>(R.gpartials, ng, ng, nv, tot, false);
-    __syncwarp();
-    if (lane_id() == 0) R.counters[ng] = 0u;
+  // the last group closes the grid: lanes over the ng group totals
+  for (int k = warp_id(); k < nv; k += nwarps) {
+    double v = 0.0;
+    for (int q = lane_id(); q < ng; q += 32) v += __ldcg(R.gpartials + k * ng + q);
+    v = warp_allsum(v);
+    if (lane_id() == 0) tot[k] = v;
   }
   __syncthreads();
+  if (threadIdx.x == 0) R.counters[ng] = 0u;
   return true;
 }
 

@@ -8,7 +8,8 @@ namespace gsk {
 // ------------------------------------------------------------------ host
 
 struct GmPlan {
-  int g_tile, g_gd, g_gb, g_gc, g_gx, wmode, KP;
+  int g_tile, g_gx, wmode, KP, nclass;
+  int g_gd[kGmClasses], g_gb[kGmClasses], g_gc[kGmClasses];
   GmArgs<double> a;
   double* wbuf;
   GmState host_state;
@@ -22,23 +23,54 @@ static void gm_launch_kp(gsk_ctx* ctx, GmPlan& P, int k, cudaStream_t s) {
     case kKUnitCheck: launch_unit_check(ctx, a.n, P.wbuf, a.red, &a.S->w_identity, s); break;
     case kKGmInit: gm_residual<double, true><<<P.g_tile, kBlock, 0, s>>>(a); break;
     case kKGmGa: gm_ga<double><<<P.g_tile, kBlock, 0, s>>>(a); break;
-    case kKGmGd: gm_gd<double, KP><<<P.g_gd, kBlock, 0, s>>>(a); break;
-    case kKGmGb: gm_gb<double, KP><<<P.g_gb, kBlock, 0, s>>>(a); break;
-    case kKGmGc: gm_gc<double, KP><<<P.g_gc, kBlock, 0, s>>>(a); break;
     case kKGmGy: gm_gy<double><<<1, 32, 0, s>>>(a); break;
     case kKGmGx: gm_gx<double, KP><<<P.g_gx, kBlock, 0, s>>>(a); break;
     case kKGmGr: gm_residual<double, false><<<P.g_tile, kBlock, 0, s>>>(a); break;
   }
 }
 
-// Grids of the basis kernels (CGS passes: two FP64 rows per thread; x
-// update: one): as many blocks as fit at each kernel's occupancy.
+// CGS passes of class c (KP = kGmClassKP[c] columns at most).
 template <int KP>
-static void gm_grids_kp(gsk_ctx* ctx, GmPlan& P, int n) {
-  P.g_gd = ctx->occ_grid((const void*)gm_gd<double, KP>, (n + 1) / 2, kBlock);
-  P.g_gb = ctx->occ_grid((const void*)gm_gb<double, KP>, (n + 1) / 2, kBlock);
-  P.g_gc = ctx->occ_grid((const void*)gm_gc<double, KP>, (n + 1) / 2, kBlock);
-  P.g_gx = ctx->occ_grid((const void*)gm_gx<double, KP>, n, kBlock);
+static void gm_launch_cgs_kp(GmPlan& P, int k, int c, cudaStream_t s) {
+  GmArgs<double>& a = P.a;
+  switch (k) {
+    case kKGmGd: gm_gd<double, KP><<<P.g_gd[c], kBlock, 0, s>>>(a); break;
+    case kKGmGb: gm_gb<double, KP><<<P.g_gb[c], kBlock, 0, s>>>(a); break;
+    // pass 3 keeps no per-column accumulators: one instance up to 32 columns
+    case kKGmGc: gm_gc<double, (KP <= 32 ? 32 : 64)><<<P.g_gc[c], kBlock, 0, s>>>(a); break;
+  }
+}
+
+static void gm_launch_cgs(GmPlan& P, int k, int c, cudaStream_t s) {
+  switch (c) {
+    case 0: gm_launch_cgs_kp<4>(P, k, c, s); break;
+    case 1: gm_launch_cgs_kp<8>(P, k, c, s); break;
+    case 2: gm_launch_cgs_kp<16>(P, k, c, s); break;
+    case 3: gm_launch_cgs_kp<32>(P, k, c, s); break;
+    default: gm_launch_cgs_kp<64>(P, k, c, s); break;
+  }
+}
+
+// Grids: CGS passes (two FP64 rows per thread) and the x update (one), as
+// many blocks as fit at each kernel's occupancy.
+template <int KP>
+static void gm_grids_class(gsk_ctx* ctx, GmPlan& P, int c, int n) {
+  const int cap = ctx->basis_per_sm;
+  P.g_gd[c] = ctx->occ_grid((const void*)gm_gd<double, KP>, (n + 1) / 2, kBlock, cap);
+  P.g_gb[c] = ctx->occ_grid((const void*)gm_gb<double, KP>, (n + 1) / 2, kBlock, cap);
+  P.g_gc[c] = ctx->occ_grid((const void*)gm_gc<double, (KP <= 32 ? 32 : 64)>, (n + 1) / 2, kBlock, cap);
+}
+
+static void gm_grids(gsk_ctx* ctx, GmPlan& P, int n) {
+  for (int c = 0; c < kGmClasses; ++c) P.g_gd[c] = P.g_gb[c] = P.g_gc[c] = 1;
+  gm_grids_class<4>(ctx, P, 0, n);
+  if (P.nclass > 1) gm_grids_class<8>(ctx, P, 1, n);
+  if (P.nclass > 2) gm_grids_class<16>(ctx, P, 2, n);
+  if (P.nclass > 3) gm_grids_class<32>(ctx, P, 3, n);
+  if (P.nclass > 4) gm_grids_class<64>(ctx, P, 4, n);
+  if (P.KP == 16) P.g_gx = ctx->occ_grid((const void*)gm_gx<double, 16>, n, kBlock);
+  else if (P.KP == 32) P.g_gx = ctx->occ_grid((const void*)gm_gx<double, 32>, n, kBlock);
+  else P.g_gx = ctx->occ_grid((const void*)gm_gx<double, 64>, n, kBlock);
 }
 
 static void gm_launch(gsk_ctx* ctx, GmPlan& P, int k, cudaStream_t s) {
@@ -58,14 +90,15 @@ static gsk_status gm_record(gsk_ctx* ctx, GmPlan& P, cudaGraphExec_t* exec_out) 
   GmArgs<double>& a = P.a;
   a.in_graph = 1;
   GSK_CK(cudaGraphConditionalHandleCreate(&a.h_outer, top, 1u, cudaGraphCondAssignDefault));
-  // top: [weights] -> init -> WHILE_outer{ WHILE_inner{ga, gb, gc} -> gy -> gx -> gr }
-  // The init kernel sets the inner handle, which is created against the
-  // outer body; so the outer node is added first (no dependencies yet), the
-  // init chain is recorded, and the edge init -> outer is added afterwards.
+  // top: [weights] -> init -> WHILE_outer{ step 0 -> ... -> step m-1 -> gy -> gx -> gr },
+  // step j = ga -> gd, gb (class of k = j + 1) -> gc.  The cycle's steps are
+  // unrolled (no inner conditional node to relaunch per step, and each step's
+  // basis kernels are fixed at record time); steps after the end of a cycle
+  // return at entry.
+  a.unrolled = 1;
   cudaGraphNode_t onode;
   cudaGraph_t obody;
   GSK_CK(add_conditional(top, {}, a.h_outer, cudaGraphCondTypeWhile, 1, &onode, &obody));
-  GSK_CK(cudaGraphConditionalHandleCreate(&a.h_inner, obody, 1u, 0));
   Capture c0;
   GSK_CK(c0.begin(cs, top));
   if (P.wmode == 0) {
@@ -78,17 +111,15 @@ static gsk_status gm_record(gsk_ctx* ctx, GmPlan& P, cudaGraphExec_t* exec_out) 
     std::vector<cudaGraphNode_t> to(c0.tail.size(), onode);
     GSK_CK(cudaGraphAddDependencies(top, c0.tail.data(), to.data(), nullptr, c0.tail.size()));
   }
-  cudaGraphNode_t inode;
-  cudaGraph_t ibody;
-  GSK_CK(add_conditional(obody, {}, a.h_inner, cudaGraphCondTypeWhile, 1, &inode, &ibody));
   Capture c1;
-  GSK_CK(c1.begin(cs, ibody));
-  for (int k : {kKGmGa, kKGmGd, kKGmGb, kKGmGc}) gm_launch(ctx, P, k, cs);
-  GSK_CK(c1.end());
-  Capture c2;
-  GSK_CK(c2.begin(cs, obody, {inode}));
+  GSK_CK(c1.begin(cs, obody));
+  for (int j = 0; j < a.m; ++j) {
+    const int c = gm_kclass(j + 1);
+    gm_launch(ctx, P, kKGmGa, cs);
+    for (int k : {kKGmGd, kKGmGb, kKGmGc}) gm_launch_cgs(P, k, c, cs);
+  }
   for (int k : {kKGmGy, kKGmGx, kKGmGr}) gm_launch(ctx, P, k, cs);
-  GSK_CK(c2.end());
+  GSK_CK(c1.end());
   GSK_CK(cudaGraphInstantiate(exec_out, top, 0));
   return GSK_OK;
 }
@@ -103,11 +134,12 @@ static gsk_status gm_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, void
   P.KP = m <= 16 ? 16 : (m <= 32 ? 32 : 64);
   // tile (SpMV) kernels carry no per-column accumulators: full occupancy
   P.g_tile = ctx->spmv_grid(n);
-  if (P.KP == 16) gm_grids_kp<16>(ctx, P, n);
-  else if (P.KP == 32) gm_grids_kp<32>(ctx, P, n);
-  else gm_grids_kp<64>(ctx, P, n);
+  P.nclass = gm_kclass(m) + 1;
+  gm_grids(ctx, P, n);
   int gmax = ctx->grid_for(n, kBlock, 8);  // unit check
-  for (int g : {P.g_tile, P.g_gd, P.g_gb, P.g_gc}) gmax = g > gmax ? g : gmax;
+  if (P.g_tile > gmax) gmax = P.g_tile;
+  for (int c = 0; c < P.nclass; ++c)
+    for (int g : {P.g_gd[c], P.g_gb[c], P.g_gc[c]}) gmax = g > gmax ? g : gmax;
   const long long ldv = ((long long)n + 63) / 64 * 64;
   GmArgs<double>& a = P.a;
   std::memset(&a, 0, sizeof(a));
@@ -192,8 +224,10 @@ gsk_status gm_profile(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, in
   while (!st.stop && !bits && st.iters < max_iters) {
     do {
       const int j = st.j;
-      for (int k : {kKGmGa, kKGmGd, kKGmGb, kKGmGc})
-        if ((s = timed(k, j)) != GSK_OK) return s;
+      if ((s = timed(kKGmGa, j)) != GSK_OK) return s;
+      for (int k : {kKGmGd, kKGmGb, kKGmGc})
+        if ((s = T.time(k, j, [&](cudaStream_t q) { gm_launch_cgs(P, k, gm_kclass(j + 1), q); })) != GSK_OK)
+          return s;
       if ((s = gm_readback(ctx, P, T.st, st, bits)) != GSK_OK) return s;
     } while (st.cont && !bits && st.iters < max_iters);
     for (int k : {kKGmGy, kKGmGx, kKGmGr})

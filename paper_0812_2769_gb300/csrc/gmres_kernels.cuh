@@ -61,7 +61,21 @@ struct GmArgs {
   int* err;
   cudaGraphConditionalHandle h_outer, h_inner;
   int in_graph;
+  // unrolled cycle: the graph holds the m steps of a cycle as a chain (step j
+  // with the basis kernels of class gm_kclass(j + 1)) instead of an inner
+  // WHILE node; once the cycle has ended (S->cont == 0) the remaining steps'
+  // kernels return at entry
+  int unrolled;
 };
+
+// Basis-kernel class of a step with k columns: the kernels of class c hold
+// per-column accumulators for up to kGmClassKP[c] columns, so small k runs
+// with few registers and many resident blocks.
+constexpr int kGmClasses = 5;
+constexpr int kGmClassKP[kGmClasses] = {4, 8, 16, 32, 64};
+__host__ __device__ __forceinline__ int gm_kclass(int k) {
+  return k <= 4 ? 0 : (k <= 8 ? 1 : (k <= 16 ? 2 : (k <= 32 ? 3 : 4)));
+}
 
 template <typename T>
 __device__ __forceinline__ void gm_set_cond(const GmArgs<T>& a, cudaGraphConditionalHandle h, unsigned v) {
@@ -73,7 +87,9 @@ __device__ __forceinline__ void gm_set_cond(const GmArgs<T>& a, cudaGraphConditi
 __device__ __forceinline__ double gm_wgt(const double* w, bool wid, int i) { return wid ? 1.0 : __ldg(w + i); }
 
 // Block sum of NV register accumulators (only the first nv are needed), in
-// chunks of 16 rows of a [16][kBlock] shared table.
+// chunks of 16 rows of a [min(NV, 16)][kBlock] shared table.
+template <int NV>
+__host__ __device__ constexpr int chunk_rows() { return NV < 16 ? NV : 16; }
 template <int NV, typename A>
 __device__ __forceinline__ void block_sum_chunked(const A (&v)[NV], int nv, double* table, double* res) {
 #pragma unroll
@@ -164,7 +180,7 @@ __global__ void __launch_bounds__(kBlock) gm_residual(GmArgs<T> a) {
     S->stop = stop;
     S->cont = !stop;
     gm_set_cond(a, a.h_outer, (unsigned)!stop);
-    gm_set_cond(a, a.h_inner, (unsigned)!stop);
+    if (!a.unrolled) gm_set_cond(a, a.h_inner, (unsigned)!stop);
   }
 }
 
@@ -175,6 +191,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) gm_ga(GmArgs<T> a) {
   __shared__ PipeSmem<T> pipe;
   const GmState* S = a.S;
+  if (a.unrolled && !S->cont) return;  // the cycle ended at an earlier step
   const int j = S->j;
   const T* vj = a.V + (long long)j * a.ldv;
   T* __restrict__ wout = a.V + (long long)(j + 1) * a.ldv;
@@ -230,8 +247,9 @@ template <typename T, int KP>
 __global__ void __launch_bounds__(kBlock) gm_gd(GmArgs<T> a) {
   using Acc = typename AccOf<T>::type;
   constexpr int R = Vec16<T>::R;
-  __shared__ double table[16 * kBlock], res[KP], tot[KP];
+  __shared__ double table[chunk_rows<KP>() * kBlock], res[KP], tot[KP];
   const GmState* S = a.S;
+  if (a.unrolled && !S->cont) return;  // the cycle ended at an earlier step
   const int j = S->j, k = j + 1;
   const T* __restrict__ wv = a.V + (long long)(j + 1) * a.ldv;
   Acc acc[KP];
@@ -267,8 +285,9 @@ __global__ void __launch_bounds__(kBlock) gm_gb(GmArgs<T> a) {
   using Acc = typename AccOf<T>::type;
   constexpr int R = Vec16<T>::R;
   __shared__ Acc coef[KP];
-  __shared__ double table[16 * kBlock], res[KP], tot[KP];
+  __shared__ double table[chunk_rows<KP>() * kBlock], res[KP], tot[KP];
   const GmState* S = a.S;
+  if (a.unrolled && !S->cont) return;  // the cycle ended at an earlier step
   const int j = S->j, k = j + 1;
   T* wv = a.V + (long long)(j + 1) * a.ldv;
   for (int c = threadIdx.x; c < k; c += kBlock) coef[c] = (Acc)(a.sig[c] * a.h1[c]);
@@ -323,6 +342,7 @@ __global__ void __launch_bounds__(kBlock) gm_gc(GmArgs<T> a) {
   __shared__ Acc coef[KP];
   __shared__ double table[kBlock], res[1], tot[1];
   GmState* S = a.S;
+  if (a.unrolled && !S->cont) return;  // the cycle ended at an earlier step
   const int j = S->j, k = j + 1;
   T* wv = a.V + (long long)(j + 1) * a.ldv;
   for (int c = threadIdx.x; c < k; c += kBlock) coef[c] = (Acc)(a.sig[c] * a.h2[c]);
@@ -409,7 +429,7 @@ __global__ void __launch_bounds__(kBlock) gm_gc(GmArgs<T> a) {
       S->j = j + 1;
     }
     S->cont = cont;
-    gm_set_cond(a, a.h_inner, (unsigned)cont);
+    if (!a.unrolled) gm_set_cond(a, a.h_inner, (unsigned)cont);
   }
 }
 

@@ -48,6 +48,10 @@ struct gsk_ctx {
   int num_sms = 0;
   // blocks per SM of the SpMV-family kernels (GSK_SPMV_BLOCKS_PER_SM, 1..5)
   int spmv_per_sm = 5;
+  // cap on blocks per SM of the GMRES basis kernels (GSK_BASIS_BLOCKS_PER_SM):
+  // more resident blocks hide less latency than they cost, as the second CGS
+  // pass re-reads the basis rows of the first from L1 (measured best: 3)
+  int basis_per_sm = 3;
   std::string last_error;
   // device workspace
   void* ws = nullptr;
@@ -80,7 +84,7 @@ struct gsk_ctx {
   // (the kernel's occupancy at kBlock threads, cached per kernel), fewer when
   // there is less work.
   std::unordered_map<const void*, int> occ_cache;
-  int occ_grid(const void* kernel, long long work_items, int per_block) {
+  int occ_grid(const void* kernel, long long work_items, int per_block, int cap_per_sm = 0) {
     auto it = occ_cache.find(kernel);
     int per_sm;
     if (it != occ_cache.end()) {
@@ -93,6 +97,7 @@ struct gsk_ctx {
       }
       occ_cache[kernel] = per_sm;
     }
+    if (cap_per_sm > 0 && per_sm > cap_per_sm) per_sm = cap_per_sm;
     return grid_for(work_items, per_block, per_sm);
   }
   int grid_for(long long work_items, int per_block, int per_sm = 8) const {
