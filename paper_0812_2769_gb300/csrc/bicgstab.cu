@@ -7,6 +7,9 @@ namespace gsk {
 
 // ------------------------------------------------------------------ host
 
+// Bi-CGSTAB iterations per pass of the graph's loop body.
+constexpr int kBcgUnroll = 4;
+
 struct BcgPlan {
   int g_tile, g_k2a, g_k3, g_k4, wmode;
   BcgArgs<double> a;
@@ -40,6 +43,7 @@ static gsk_status bcg_record(gsk_ctx* ctx, BcgPlan& P, cudaGraphExec_t* exec_out
   } guard{top};
   BcgArgs<double>& a = P.a;
   a.in_graph = 1;
+  a.unrolled = 1;
   GSK_CK(cudaGraphConditionalHandleCreate(&a.h_while, top, 1u, cudaGraphCondAssignDefault));
 
   Capture c0;
@@ -54,25 +58,17 @@ static gsk_status bcg_record(gsk_ctx* ctx, BcgPlan& P, cudaGraphExec_t* exec_out
   cudaGraphNode_t wnode;
   cudaGraph_t wbody;
   GSK_CK(add_conditional(top, c0.tail, a.h_while, cudaGraphCondTypeWhile, 1, &wnode, &wbody));
-  GSK_CK(cudaGraphConditionalHandleCreate(&a.h_if, wbody, 0u, 0));
 
+  // loop body: kBcgUnroll iterations (k1, k2a, k2b, k3, k4) in a row, then the
+  // true-residual check and finish (kt, kr), which return at entry unless an
+  // iteration set check or stop; no conditional node inside the body
   Capture c1;
   GSK_CK(c1.begin(cs, wbody));
-  for (int k : {kKBcgK1, kKBcgK2a, kKBcgK2b, kKBcgK3}) bcg_launch(ctx, P, k, cs);
-  GSK_CK(c1.end());
-
-  cudaGraphNode_t inode;
-  cudaGraph_t ib[2];
-  GSK_CK(add_conditional(wbody, c1.tail, a.h_if, cudaGraphCondTypeIf, 2, &inode, ib));
-  Capture c2;
-  GSK_CK(c2.begin(cs, ib[0]));
+  for (int u = 0; u < kBcgUnroll; ++u)
+    for (int k : {kKBcgK1, kKBcgK2a, kKBcgK2b, kKBcgK3, kKBcgK4}) bcg_launch(ctx, P, k, cs);
   bcg_launch(ctx, P, kKBcgKt, cs);
   bcg_launch(ctx, P, kKBcgKr, cs);
-  GSK_CK(c2.end());
-  Capture c3;
-  GSK_CK(c3.begin(cs, ib[1]));
-  bcg_launch(ctx, P, kKBcgK4, cs);
-  GSK_CK(c3.end());
+  GSK_CK(c1.end());
 
   GSK_CK(cudaGraphInstantiate(exec_out, top, 0));
   return GSK_OK;
@@ -122,6 +118,7 @@ static gsk_status bcg_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, voi
   P.a.x = (double*)x;
   P.a.w = P.wmode == 0 ? P.wbuf : (P.wmode == 2 ? opts.weights : nullptr);
   P.a.in_graph = 0;
+  P.a.unrolled = 0;
   P.a.h_while = P.a.h_if = 0;
   P.a.vec_ok = ((uintptr_t)x % 16 == 0) && (P.a.w == nullptr || (uintptr_t)P.a.w % 16 == 0);
   BcgState& hs = P.host_state;

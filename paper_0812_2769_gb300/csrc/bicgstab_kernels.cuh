@@ -52,6 +52,10 @@ struct BcgArgs {
   int* err;
   cudaGraphConditionalHandle h_while, h_if;
   int in_graph;
+  // unrolled loop body: the graph holds several iterations k1..k4 in a row,
+  // then kt, kr, without an IF node; once an iteration has set check or stop
+  // the following kernels return at entry
+  int unrolled;
   int vec_ok;  // x (and w, if any) are 16-byte aligned: 128-bit loads allowed
 };
 
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(kBlock) bcg_init(BcgArgs<T> a) {
 template <typename T>
 __global__ void __launch_bounds__(kBlock) bcg_k1(BcgArgs<T> a) {
   BcgState* S = a.S;
-  if (S->stop) return;
+  if (S->stop || S->check) return;
   __shared__ PipeSmem<T> pipe;
   __shared__ double blk[2], tot[2];
   double* sm = reinterpret_cast<double*>(&pipe);  // reduction scratch after the product
@@ -191,7 +195,7 @@ __device__ __forceinline__ Acc bcg_k2a_rows(const BcgArgs<T>& a, Acc alpha) {
 template <typename T>
 __global__ void __launch_bounds__(kBlock) bcg_k2a(BcgArgs<T> a) {
   BcgState* S = a.S;
-  if (S->stop) return;
+  if (S->stop || S->check) return;
   __shared__ double sm[1 * kBlock], blk[1], tot[1];
   using Acc = typename AccOf<T>::type;
   const Acc alpha = (Acc)S->alpha;
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(kBlock) bcg_k2a(BcgArgs<T> a) {
 template <typename T>
 __global__ void __launch_bounds__(kBlock) bcg_k2b(BcgArgs<T> a) {
   BcgState* S = a.S;
-  if (S->stop || S->halfexit) return;
+  if (S->stop || S->check || S->halfexit) return;
   __shared__ PipeSmem<T> pipe;
   __shared__ double blk[2], tot[2];
   double* sm = reinterpret_cast<double*>(&pipe);  // reduction scratch after the product
@@ -289,6 +293,7 @@ __device__ __forceinline__ void bcg_k3_rows(const BcgArgs<T>& a, Acc alpha, Acc 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) bcg_k3(BcgArgs<T> a) {
   BcgState* S = a.S;
+  if (a.unrolled && (S->stop || S->check)) return;
   if (S->stop) {
     if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(a, a.h_if, 1u);
     return;
@@ -302,7 +307,7 @@ __global__ void __launch_bounds__(kBlock) bcg_k3(BcgArgs<T> a) {
       S->iters += 1;
       S->mu_rec = S->mu_s;
       S->check = 1;
-      set_cond(a, a.h_if, 1u);
+      if (!a.unrolled) set_cond(a, a.h_if, 1u);
     }
     return;
   }
@@ -340,7 +345,7 @@ __global__ void __launch_bounds__(kBlock) bcg_k3(BcgArgs<T> a) {
     }
     S->check = check;
     S->stop = stop;
-    set_cond(a, a.h_if, (unsigned)(check | stop));
+    if (!a.unrolled) set_cond(a, a.h_if, (unsigned)(check | stop));
   }
 }
 
@@ -372,7 +377,7 @@ __global__ void __launch_bounds__(kBlock) bcg_k4(BcgArgs<T> a) {
 template <typename T>
 __global__ void __launch_bounds__(kBlock) bcg_kt(BcgArgs<T> a) {
   BcgState* S = a.S;
-  if (!(S->check || S->stop)) return;  // the graph's IF node already excludes this
+  if (!(S->check || S->stop)) return;  // nothing to confirm yet
   __shared__ PipeSmem<T> pipe;
   __shared__ double blk[2], tot[2];
   double* sm = reinterpret_cast<double*>(&pipe);  // reduction scratch after the product
@@ -396,7 +401,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) bcg_kr(BcgArgs<T> a) {
   BcgState* S = a.S;
   const int stop = S->stop, check = S->check;
-  if (!(check || stop)) return;  // the graph's IF node already excludes this
+  if (!(check || stop)) return;  // nothing to confirm yet
   const bool met = S->mu_true < S->tol;
   const bool refresh = !stop && check && !met && S->refresh_left > 0 && *(volatile int*)a.err == 0;
   if (refresh) {
