@@ -68,9 +68,9 @@ static void gm_grids(gsk_ctx* ctx, GmPlan& P, int n) {
   if (P.nclass > 2) gm_grids_class<16>(ctx, P, 2, n);
   if (P.nclass > 3) gm_grids_class<32>(ctx, P, 3, n);
   if (P.nclass > 4) gm_grids_class<64>(ctx, P, 4, n);
-  if (P.KP == 16) P.g_gx = ctx->occ_grid((const void*)gm_gx<double, 16>, n, kBlock);
-  else if (P.KP == 32) P.g_gx = ctx->occ_grid((const void*)gm_gx<double, 32>, n, kBlock);
-  else P.g_gx = ctx->occ_grid((const void*)gm_gx<double, 64>, n, kBlock);
+  if (P.KP == 16) P.g_gx = ctx->occ_grid((const void*)gm_gx<double, 16>, (n + 1) / 2, kBlock, ctx->basis_per_sm);
+  else if (P.KP == 32) P.g_gx = ctx->occ_grid((const void*)gm_gx<double, 32>, (n + 1) / 2, kBlock, ctx->basis_per_sm);
+  else P.g_gx = ctx->occ_grid((const void*)gm_gx<double, 64>, (n + 1) / 2, kBlock, ctx->basis_per_sm);
 }
 
 static void gm_launch(gsk_ctx* ctx, GmPlan& P, int k, cudaStream_t s) {
@@ -176,6 +176,7 @@ static gsk_status gm_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, void
   a.x = (double*)x;
   a.w = P.wmode == 0 ? P.wbuf : (P.wmode == 2 ? opts.weights : nullptr);
   a.in_graph = 0;
+  a.vec_ok = ((uintptr_t)x % 16) == 0;
   GmState& hs = P.host_state;
   std::memset(&hs, 0, sizeof(hs));
   hs.tol = tol;
@@ -231,7 +232,7 @@ gsk_status gm_profile(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, in
       if ((s = gm_readback(ctx, P, T.st, st, bits)) != GSK_OK) return s;
     } while (st.cont && !bits && st.iters < max_iters);
     for (int k : {kKGmGy, kKGmGx, kKGmGr})
-      if ((s = timed(k, -1)) != GSK_OK) return s;
+      if ((s = timed(k, k == kKGmGr ? -1 : st.kcols - 1)) != GSK_OK) return s;
     if ((s = gm_readback(ctx, P, T.st, st, bits)) != GSK_OK) return s;
   }
   if (info) *info = gsk_info{st.iters, st.restarts, 0, 0, st.conv, st.mu_true, st.est, 0.f};

@@ -61,6 +61,7 @@ struct GmArgs {
   int* err;
   cudaGraphConditionalHandle h_outer, h_inner;
   int in_graph;
+  int vec_ok;  // x is 16-byte aligned: 128-bit loads in the x update
   // unrolled cycle: the graph holds the m steps of a cycle as a chain (step j
   // with the basis kernels of class gm_kclass(j + 1)) instead of an inner
   // WHILE node; once the cycle has ended (S->cont == 0) the remaining steps'
@@ -433,29 +434,63 @@ __global__ void __launch_bounds__(kBlock) gm_gc(GmArgs<T> a) {
   }
 }
 
-// Back substitution H(0:k, 0:k) y = g(0:k), row by row as in the definition.
+// Back substitution H(0:k, 0:k) y = g(0:k), bottom row first, by one warp:
+// the triangle is staged in shared memory and each row's sum is split over
+// the lanes (a fixed shuffle tree).
 template <typename T>
 __global__ void gm_gy(GmArgs<T> a) {
-  if (threadIdx.x != 0) return;
-  const int k = a.S->kcols, ld = a.m + 1;
-  for (int i = k - 1; i >= 0; --i) {
-    double s = a.g[i];
-    for (int q = i + 1; q < k; ++q) s -= a.H[(long long)q * ld + i] * a.y[q];
-    a.y[i] = s / a.H[(long long)i * ld + i];
+  __shared__ double Hs[kMaxM * kMaxM];
+  __shared__ double ys[kMaxM], gs[kMaxM];
+  const int k = a.S->kcols, ld = a.m + 1, lane = lane_id();
+  if (threadIdx.x >= 32) return;
+  for (int e = lane; e < k * k; e += 32) {
+    const int col = e / k, row = e - col * k;
+    if (row <= col) Hs[row * kMaxM + col] = a.H[(long long)col * ld + row];
   }
+  for (int i = lane; i < k; i += 32) gs[i] = a.g[i];
+  __syncwarp();
+  for (int i = k - 1; i >= 0; --i) {
+    double s = 0.0;
+    for (int q = i + 1 + lane; q < k; q += 32) s = fma(Hs[i * kMaxM + q], ys[q], s);
+    s = warp_allsum(s);
+    if (lane == 0) ys[i] = (gs[i] - s) / Hs[i * kMaxM + i];
+    __syncwarp();
+  }
+  for (int i = lane; i < k; i += 32) a.y[i] = ys[i];
 }
 
-// x += V_k (sig .* y).
+// x += V_k (sig .* y): two rows per thread (128-bit loads of every basis
+// column; the caller's x must be 16-byte aligned for that, else scalar), the
+// columns in order for each row.
 template <typename T, int KP>
 __global__ void __launch_bounds__(kBlock) gm_gx(GmArgs<T> a) {
   __shared__ double coef[KP];
   const int k = a.S->kcols;
   for (int c = threadIdx.x; c < k; c += kBlock) coef[c] = a.sig[c] * a.y[c];
   __syncthreads();
-  GM_ROW_LOOP(a) {
-    double x = (double)a.x[i];
-    for_columns<KP>(k, [&](int c) { x = fma((double)a.V[(long long)c * a.ldv + i], coef[c], x); });
-    a.x[i] = (T)x;
+  constexpr int R = Vec16<T>::R;
+  GM_VEC_LOOP(a, R) {
+    if (i0 + R <= a.n && a.vec_ok) {
+      const Vec16<T> x0 = vload(a.x + i0);
+      double x[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[r] = (double)x0.v[r];
+      for_columns<KP>(k, [&](int c) {
+        const Vec16<T> v = vload(a.V + (long long)c * a.ldv + i0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = fma((double)v.v[r], coef[c], x[r]);
+      });
+      Vec16<T> xo;
+#pragma unroll
+      for (int r = 0; r < R; ++r) xo.v[r] = (T)x[r];
+      vstore(a.x + i0, xo);
+    } else {
+      for (int i = i0; i < min(i0 + R, a.n); ++i) {
+        double x = (double)a.x[i];
+        for_columns<KP>(k, [&](int c) { x = fma((double)a.V[(long long)c * a.ldv + i], coef[c], x); });
+        a.x[i] = (T)x;
+      }
+    }
   }
 }
 
