@@ -45,6 +45,7 @@ def lib():
         L = C.CDLL(_build())
         vp = C.c_void_p
         L.or_gs_scale.argtypes = [C.c_int, _ip, _ip, _dp, vp, C.c_double, vp]
+        L.or_gs_scale_sym.argtypes = [C.c_int, _ip, _ip, _dp, vp, C.c_double, _dp, vp]
         L.or_spmv.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp]
         L.or_metric_weights.argtypes = [C.c_int, _ip, _dp, _dp]
         L.or_arnoldi.argtypes = [C.c_int, _ip, _ip, _dp, _dp, C.c_int, _dp, _dp]
@@ -80,6 +81,20 @@ def gs_scale(rowptr, colidx, val, b=None, p=2.0):
     d = np.empty(n)
     _check(lib().or_gs_scale(n, rowptr, colidx, val, _ptr(bb), float(p), _ptr(d)))
     return val, bb, d
+
+
+def gs_scale_sym(rowptr, colidx, val, b=None, p=2.0):
+    """Two-sided GS (Sec. 2): returns (D^1/2 A D^1/2 values, D^1/2 b or None,
+    s, w) with s_i = (1/||a_i||_p)^(1/2) and w the stopping-metric weights
+    of the scaled system (w_i = (1/||a_i||_2) / s_i)."""
+    rowptr, colidx, val = _csr(rowptr, colidx, val)
+    val = val.copy()
+    n = len(rowptr) - 1
+    bb = None if b is None else np.array(b, dtype=np.float64)
+    s = np.empty(n)
+    w = np.empty(n)
+    _check(lib().or_gs_scale_sym(n, rowptr, colidx, val, _ptr(bb), float(p), s, _ptr(w)))
+    return val, bb, s, w
 
 
 def spmv(rowptr, colidx, val, x):

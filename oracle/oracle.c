@@ -11,6 +11,7 @@
  *
  * Sources (section / equation of the paper, Gordon & Gordon 2009):
  *   GS(p)      Sec. 1 and Sec. 2, Eq. (2): D = diag(1/||a_i||_p), solve DAx = Db.
+ *   D^(1/2)    Sec. 2 (two-sided variant): D^(1/2) A D^(1/2) y = D^(1/2) b.
  *   L_p norm   Sec. 2 (read with absolute values; p = inf is max |a_ij|).
  *   GMRES(m)   Sec. 2: restarted GMRES (Saad & Schultz 1986) with double
  *              classical Gram-Schmidt; Givens rotations for the least-squares
@@ -93,6 +94,40 @@ int or_gs_scale(int n, const int* rowptr, const int* colidx, double* val,
     for (int k = 0; k < len; ++k) val[r0 + k] = val[r0 + k] / nrm;
     if (b) b[i] = b[i] / nrm;
     if (s_out) s_out[i] = 1.0 / nrm;
+  }
+  return OR_OK;
+}
+
+/* Two-sided variant of GS (Sec. 2, the paragraph after the experimental
+ * set-up): with D = diag(1/||a_i||_p), the system becomes
+ * D^(1/2) A D^(1/2) y = D^(1/2) b, and x = D^(1/2) y.
+ *   s_out[i] = (1/||a_i||_p)^(1/2), the diagonal of D^(1/2) (required);
+ *   w_out[i] = (1/||a_i||_2) / s_out[i] (optional): stopping-metric weights
+ *   for the scaled system.  Its residual is D^(1/2)(b - A x), so these
+ *   weights turn its norm into the GS(2)-scaled residual of the original
+ *   system, the paper's stopping test (Sec. 2.2).
+ * The whole input is checked (finite values, column indices, no zero row)
+ * before anything is written. */
+int or_gs_scale_sym(int n, const int* rowptr, const int* colidx, double* val,
+                    double* b, double p, double* s_out, double* w_out) {
+  if (n < 0 || !(p >= 1.0) || !s_out) return OR_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      if (colidx[k] < 0 || colidx[k] >= n) return OR_ERR_ARG;
+      if (!isfinite(val[k])) return OR_ERR_NONFINITE;
+    }
+    if (b && !isfinite(b[i])) return OR_ERR_NONFINITE;
+  }
+  for (int i = 0; i < n; ++i) {
+    int r0 = rowptr[i], len = rowptr[i + 1] - rowptr[i];
+    double nrm = row_norm(val + r0, len, p);
+    if (nrm == 0.0) return OR_ERR_ZERO_ROW;
+    s_out[i] = sqrt(1.0 / nrm);
+    if (w_out) w_out[i] = (1.0 / row_norm(val + r0, len, 2.0)) / s_out[i];
+  }
+  for (int i = 0; i < n; ++i) {
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) val[k] = val[k] * s_out[i] * s_out[colidx[k]];
+    if (b) b[i] = b[i] * s_out[i];
   }
   return OR_OK;
 }

@@ -108,6 +108,88 @@ def test_gs_errors():
         oracle.gs_scale(rp, ci, np.abs(va), None, 0.5)
 
 
+# ------------------------------------------------- two-sided D^(1/2) scaling
+def _dense_of(rp, ci, va, n):
+    M = np.zeros((n, n))
+    for i in range(n):
+        M[i, ci[rp[i]:rp[i + 1]]] = va[rp[i]:rp[i + 1]]
+    return M
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0, math.inf])
+def test_sym_scaling_solves_the_original_system(p):
+    """Sec. 2: D^1/2 A D^1/2 y = D^1/2 b and x = D^1/2 y solve A x = b."""
+    s = configs.c1(12)
+    x0 = np.linalg.solve(s.dense(), s.b)
+    val, b, sv, _ = oracle.gs_scale_sym(s.rowptr, s.colidx, s.val, s.b, p)
+    y = np.linalg.solve(_dense_of(s.rowptr, s.colidx, val, s.n), b)
+    assert np.allclose(sv * y, x0, rtol=1e-11, atol=1e-12)
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0, math.inf])
+def test_sym_scaling_is_similar_to_gs(p):
+    """D^1/2 A D^1/2 = D^-1/2 (D A) D^1/2: the same eigenvalues as GS(p)(A)."""
+    A, rp, ci, va = _random_csr(16, 7)
+    v_gs, _, _ = oracle.gs_scale(rp, ci, va, None, p)
+    v_sym, _, _, _ = oracle.gs_scale_sym(rp, ci, va, None, p)
+    e_gs = np.sort_complex(np.linalg.eigvals(_dense_of(rp, ci, v_gs, 16)))
+    e_sym = np.sort_complex(np.linalg.eigvals(_dense_of(rp, ci, v_sym, 16)))
+    assert np.allclose(e_gs, e_sym, rtol=1e-10, atol=1e-12)
+
+
+def test_sym_scaling_closed_forms():
+    # a diagonal matrix becomes its sign pattern; a symmetric one stays symmetric
+    n = 5
+    d = np.array([3.0, -0.5, 7.0, -2.0, 1e-3])
+    rp = np.arange(n + 1, dtype=np.int32)
+    ci = np.arange(n, dtype=np.int32)
+    for p in (1.0, 2.0, math.inf):
+        v, _, sv, _ = oracle.gs_scale_sym(rp, ci, d, None, p)
+        assert np.allclose(v, np.sign(d), rtol=4 * EPS, atol=0)  # d * s * s rounds within a few ulp
+        assert np.allclose(sv, 1.0 / np.sqrt(np.abs(d)), rtol=2 * EPS)
+    A, rp, ci, va = _random_csr(12, 9)
+    S = A + A.T
+    rp2 = np.zeros(13, dtype=np.int32)
+    cols, vals = [], []
+    for i in range(12):
+        nz = np.nonzero(S[i])[0]
+        cols.extend(nz)
+        vals.extend(S[i, nz])
+        rp2[i + 1] = len(cols)
+    v, _, _, _ = oracle.gs_scale_sym(rp2, np.array(cols, dtype=np.int32), np.array(vals), None, 2.0)
+    M = _dense_of(rp2, np.array(cols, dtype=np.int32), v, 12)
+    assert np.allclose(M, M.T, rtol=4 * EPS, atol=0)
+
+
+def test_sym_scaling_metric_weights_give_the_gs2_residual():
+    """Sec. 2.2: the stopping test is the GS(2)-scaled residual of the
+    original system; with the weights w, the scaled system's residual norm
+    is exactly that for x = D^1/2 y."""
+    A, rp, ci, va = _random_csr(20, 11)
+    b = np.random.default_rng(1).normal(size=20)
+    val, bs, sv, w = oracle.gs_scale_sym(rp, ci, va, b, 1.0)
+    y = np.random.default_rng(2).normal(size=20)
+    r_scaled = bs - _dense_of(rp, ci, val, 20) @ y
+    r_orig = b - A @ (sv * y)
+    d2 = 1.0 / np.linalg.norm(A, axis=1)
+    assert np.allclose(w * r_scaled, d2 * r_orig, rtol=1e-12, atol=1e-13)
+
+
+def test_sym_scaling_errors():
+    A, rp, ci, va = _random_csr(6, 0, zero_row=3)
+    with pytest.raises(oracle.OracleError, match="zero row"):
+        oracle.gs_scale_sym(rp, ci, va, None, 2.0)
+    A, rp, ci, va = _random_csr(6, 0)
+    bad = ci.copy()
+    bad[4] = 6
+    with pytest.raises(oracle.OracleError, match="invalid"):
+        oracle.gs_scale_sym(rp, bad, va, None, 2.0)
+    va2 = va.copy()
+    va2[1] = np.inf
+    with pytest.raises(oracle.OracleError, match="non-finite"):
+        oracle.gs_scale_sym(rp, ci, va2, None, 2.0)
+
+
 # ------------------------------------------------------------------ SpMV
 def test_spmv_matches_dense():
     A, rp, ci, va = _random_csr(37, 3)
