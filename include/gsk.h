@@ -167,6 +167,33 @@ gsk_status gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, 
 gsk_status gs_scale_static(gsk_csr* A, void* b, double p, double* d_out, void* stream);
 
 /*
+ * gs_scale_sym -- the two-sided variant of geometric scaling the paper also
+ * tried (Sec. 2, after the description of the experiments): with
+ * D = diag(1/||a_i||_p), A becomes D^(1/2) A D^(1/2) and b becomes
+ * D^(1/2) b.  The scaled system's solution is y = D^(-1/2) x; recover x with
+ * gsk_diag_mul(s_out, y).
+ *   A      in/out: values scaled in place (FP64 or FP32): a_ij s_i s_j
+ *   b      in/out: device [n], A's dtype, scaled in place (b_i s_i); may be NULL
+ *   p      >= 1, or INFINITY
+ *   s_out  required device FP64 [n]: s_i = (1/||a_i||_p)^(1/2)
+ *   w_out  optional device FP64 [n]: w_i = (1/||a_i||_2) / s_i.  Passed as
+ *          gsk_opts.weights to a solver of the scaled system, it makes the
+ *          stopping metric the GS(2)-scaled residual of the ORIGINAL system
+ *          (Sec. 2.2), since the scaled residual is D^(1/2)(b - A x).
+ * Errors: GSK_ERR_ARG (p < 1, bad sizes/pointers, a column index outside
+ * [0, n)), GSK_ERR_ZERO_ROW, GSK_ERR_NONFINITE; on error A and b are left
+ * unmodified.  Synchronises `stream` to read the error flags back.
+ */
+gsk_status gs_scale_sym(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* s_out, double* w_out, void* stream);
+
+/*
+ * gsk_diag_mul -- x_i <- s_i x_i for i < n (x of dtype, s FP64; device
+ * pointers).  With s from gs_scale_sym it turns the scaled system's solution
+ * y into x = D^(1/2) y (Sec. 2).  Asynchronous on `stream`.
+ */
+gsk_status gsk_diag_mul(gsk_ctx* ctx, int n, const double* s, void* x, gsk_dtype dtype, void* stream);
+
+/*
  * gsk_spmv -- y = A x, the product every Krylov step performs (Sec. 2).
  *   x, y   device [n] of A's dtype; x and y must not overlap.
  * Asynchronous on `stream`.
@@ -179,7 +206,7 @@ gsk_status gsk_spmv(gsk_ctx* ctx, const gsk_csr* A, const void* x, void* y, void
  *   b      device [n], A's dtype
  *   x      in: initial guess x0 (zeros = the paper's u0 = 0, Sec. 2.1);
  *          out: solution.  Device [n], A's dtype.
- *   m      Krylov dimension per cycle, 1..256
+ *   m      Krylov dimension per cycle, 1..64
  *   tol    stop when ||W(b-Ax)||/||W(b-Ax0)|| < tol (Sec. 2.2)
  *   opts   NULL for defaults
  *   info   host pointer or NULL; when non-NULL the call synchronises `stream`

@@ -78,6 +78,9 @@ SIGNATURES = {
     "gsk_opts_default": ([C.POINTER(OptsC)], None),
     "gs_scale": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p], C.c_int),
     "gs_scale_static": ([C.POINTER(CsrC), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p], C.c_int),
+    "gs_scale_sym": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p],
+                     C.c_int),
+    "gsk_diag_mul": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "gsk_spmv": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gmres_solve": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                      C.POINTER(OptsC), C.POINTER(InfoC), C.c_void_p], C.c_int),
@@ -237,6 +240,37 @@ def gs_scale_static(A: Csr, b=None, p: float = 2.0, d_out=None, stream=None):
     if st != OK:
         raise GskError(st, "gs_scale_static failed")
     return d_out
+
+
+def gs_scale_sym(A: Csr, b=None, p: float = 2.0, weights: bool = False, s_out=None, w_out=None,
+                 ctx: Context | None = None, stream=None):
+    """Two-sided scaling in place (Sec. 2): A <- D^1/2 A D^1/2, b <- D^1/2 b
+    with D = diag(1/||a_i||_p).  Returns (s, w): s = diag(D^1/2), so that
+    diag_mul(s, y) turns the scaled system's solution y into x; with
+    weights=True (or a w_out buffer) also w, the stopping-metric weights that
+    make a solve of the scaled system stop on the GS(2)-scaled residual of
+    the original system (pass opts(weights=w)); else w is None."""
+    import torch
+
+    ctx = ctx or default_context(A.val.device.index or 0)
+    if s_out is None:
+        s_out = torch.empty(A.n, dtype=torch.float64, device=A.val.device)
+    if w_out is None and weights:
+        w_out = torch.empty(A.n, dtype=torch.float64, device=A.val.device)
+    Ac = A.c()
+    ctx.check(lib().gs_scale_sym(ctx.handle, C.byref(Ac), _ptr(b), float(p), _ptr(s_out), _ptr(w_out),
+                                 _stream_ptr(stream)))
+    return s_out, w_out
+
+
+def diag_mul(s, x, ctx: Context | None = None, stream=None):
+    """x <- s * x on the device (x FP64 or FP32, s FP64)."""
+    import torch
+
+    ctx = ctx or default_context(x.device.index or 0)
+    dt = F64 if x.dtype == torch.float64 else F32
+    ctx.check(lib().gsk_diag_mul(ctx.handle, int(x.numel()), _ptr(s), _ptr(x), dt, _stream_ptr(stream)))
+    return x
 
 
 def gsk_spmv(A: Csr, x, y, ctx: Context | None = None, stream=None):

@@ -124,6 +124,24 @@ gsk_status gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, 
   return gsk::run_gs_scale(ctx, A, b, p, d_out, (cudaStream_t)stream);
 }
 
+gsk_status gs_scale_sym(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* s_out, double* w_out, void* stream) {
+  if (!ctx) return GSK_ERR_ARG;
+  gsk_status s = gsk::check_csr(ctx, A);
+  if (s != GSK_OK) return s;
+  if (!(p >= 1.0)) return ctx->fail(GSK_ERR_ARG, "p must be >= 1 or INFINITY");
+  if (A->n > 0 && (!A->colidx || !s_out)) return ctx->fail(GSK_ERR_ARG, "NULL colidx or s_out");
+  if (A->n == 0) return GSK_OK;
+  return gsk::run_gs_scale_sym(ctx, A, b, p, s_out, w_out, (cudaStream_t)stream);
+}
+
+gsk_status gsk_diag_mul(gsk_ctx* ctx, int n, const double* s, void* x, gsk_dtype dtype, void* stream) {
+  if (!ctx) return GSK_ERR_ARG;
+  if (n < 0 || (n > 0 && (!s || !x)) || (dtype != GSK_F64 && dtype != GSK_F32))
+    return ctx->fail(GSK_ERR_ARG, "bad n, s, x or dtype");
+  if (n == 0) return GSK_OK;
+  return gsk::launch_diag_mul(ctx, n, s, x, dtype, (cudaStream_t)stream);
+}
+
 gsk_status gsk_spmv(gsk_ctx* ctx, const gsk_csr* A, const void* x, void* y, void* stream) {
   if (!ctx) return GSK_ERR_ARG;
   gsk_status s = gsk::check_csr(ctx, A);

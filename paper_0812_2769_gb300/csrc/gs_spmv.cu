@@ -182,6 +182,104 @@ gsk_status run_gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_o
   return err_bits_status(ctx, *hbits);
 }
 
+// ------------------------------------------------ two-sided D^(1/2) scaling
+//
+// The variant the paper also tried (Sec. 2): with D = diag(1/||a_i||_p),
+// solve D^(1/2) A D^(1/2) y = D^(1/2) b and recover x = D^(1/2) y.  gs_norm
+// gives d_i = 1/||a_i||_p (and the GS(2) scales when the metric weights are
+// wanted), sym_check validates the column indices, and sym_apply scales
+// a_ij by s_i s_j only if no error was recorded, so that A and b are left
+// untouched on error.
+
+// Column indices must lie in [0, n): the column scale s_j is gathered.
+__global__ void __launch_bounds__(kBlock) sym_check_kernel(int nnz, int n, const int* __restrict__ colidx, int* err) {
+  for (int k = blockIdx.x * kBlock + threadIdx.x; k < nnz; k += gridDim.x * kBlock)
+    if ((unsigned)__ldg(colidx + k) >= (unsigned)n) atomicOr(err, kErrIndex);
+}
+
+// s_i = sqrt(d_i); w_i = d2_i / s_i (d2 = d for p = 2, else the GS(2) scales
+// already stored in w).
+__global__ void __launch_bounds__(kBlock) sym_prep_kernel(int n, const double* __restrict__ d, double* __restrict__ s,
+                                                          double* w, int w_is_d) {
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+    const double si = sqrt(d[i]);
+    s[i] = si;
+    if (w) w[i] = (w_is_d ? d[i] : w[i]) / si;
+  }
+}
+
+// a_ij <- a_ij s_i s_j, b_i <- b_i s_i; one row per thread.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) sym_apply_kernel(int n, const int* __restrict__ rowptr,
+                                                           const int* __restrict__ colidx, T* __restrict__ val,
+                                                           T* __restrict__ b, const double* __restrict__ s,
+                                                           const int* err) {
+  if (*(volatile const int*)err != 0) return;  // leave A and b as they are
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+    const double si = s[i];
+    for (int k = __ldg(rowptr + i); k < __ldg(rowptr + i + 1); ++k)
+      val[k] = (T)((double)val[k] * si * __ldg(s + __ldg(colidx + k)));
+    if (b) b[i] = (T)((double)b[i] * si);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) diag_mul_kernel(int n, const double* __restrict__ s, T* __restrict__ x) {
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) x[i] = (T)((double)x[i] * s[i]);
+}
+
+gsk_status run_gs_scale_sym(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* s_out, double* w_out,
+                            cudaStream_t st) {
+  const int pmode = p == 1.0 ? kP1 : (p == 2.0 ? kP2 : (p > 1e300 ? kPInf : kPGen));
+  const int n = A->n;
+  Arena a;
+  a.take<int>(64);
+  a.take<double>(n);
+  gsk_status s = ctx->reserve(a.off);
+  if (s != GSK_OK) return s;
+  a = Arena{(char*)ctx->ws, ctx->ws_bytes, 0};
+  int* err = a.take<int>(64);
+  double* d = a.take<double>(n);
+  GSK_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+  const int gt = ctx->grid_for((n + 31) / 32, kWarpsPerBlock, 8);
+  const int gr = ctx->grid_for(n, kBlock, 8);
+  const int gn = ctx->grid_for(A->nnz, kBlock, 8);
+  const bool w_is_d = pmode == kP2;
+  if (A->dtype == GSK_F64) {
+    gs_norm_kernel<double><<<gt, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const double*)A->val,
+                                                   (const double*)b, pmode, p, d, err);
+    if (w_out && !w_is_d)
+      gs_norm_kernel<double><<<gt, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const double*)A->val, nullptr, kP2,
+                                                     2.0, w_out, err);
+  } else {
+    gs_norm_kernel<float><<<gt, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const float*)A->val, (const float*)b,
+                                                  pmode, p, d, err);
+    if (w_out && !w_is_d)
+      gs_norm_kernel<float><<<gt, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const float*)A->val, nullptr, kP2, 2.0,
+                                                    w_out, err);
+  }
+  if (A->nnz > 0) sym_check_kernel<<<gn, kBlock, 0, st>>>(A->nnz, n, A->colidx, err);
+  sym_prep_kernel<<<gr, kBlock, 0, st>>>(n, d, s_out, w_out, w_is_d ? 1 : 0);
+  if (A->dtype == GSK_F64)
+    sym_apply_kernel<double><<<gr, kBlock, 0, st>>>(n, A->rowptr, A->colidx, (double*)A->val, (double*)b, s_out,
+                                                     err);
+  else
+    sym_apply_kernel<float><<<gr, kBlock, 0, st>>>(n, A->rowptr, A->colidx, (float*)A->val, (float*)b, s_out, err);
+  GSK_CK(cudaGetLastError());
+  int* hbits = (int*)ctx->host_pinned;
+  GSK_CK(cudaMemcpyAsync(hbits, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GSK_CK(cudaStreamSynchronize(st));
+  return err_bits_status(ctx, *hbits);
+}
+
+gsk_status launch_diag_mul(gsk_ctx* ctx, int n, const double* s, void* x, gsk_dtype dtype, cudaStream_t st) {
+  const int g = ctx->grid_for(n, kBlock, 8);
+  if (dtype == GSK_F64) diag_mul_kernel<double><<<g, kBlock, 0, st>>>(n, s, (double*)x);
+  else diag_mul_kernel<float><<<g, kBlock, 0, st>>>(n, s, (float*)x);
+  GSK_CK(cudaGetLastError());
+  return GSK_OK;
+}
+
 }  // namespace gsk
 
 // --------------------------------------------------- allocation-free GS(p)

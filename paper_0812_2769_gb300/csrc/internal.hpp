@@ -206,6 +206,9 @@ void launch_gs_norm(gsk_ctx* ctx, int n, int nnz, const int* rowptr, const doubl
                     int* err, cudaStream_t st);
 void launch_unit_check(gsk_ctx* ctx, int n, const double* w, const GridRed& red, int* out, cudaStream_t st);
 gsk_status run_gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, cudaStream_t st);
+gsk_status run_gs_scale_sym(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* s_out, double* w_out,
+                            cudaStream_t st);
+gsk_status launch_diag_mul(gsk_ctx* ctx, int n, const double* s, void* x, gsk_dtype dtype, cudaStream_t st);
 
 }  // namespace gsk
 

@@ -7,7 +7,8 @@ Problem 1 (Sec. 3): 128x128, b = A (1,...,1)^T; Table 1 (a = b = 1e3 on
 (a = b = 1000 everywhere).  Problem 4 (Sec. 6): Table 4 (80^3, D = 1e4 and
 1e6, convection 100) and Table "limit" (40^3, D = 1e4, convection 100, 200,
 500, 1000).  Every case is solved with Bi-CGSTAB and with restarted
-GMRES(10), on the original system and after GS(2), to the relative residual
+GMRES(10), on the original system, after GS(2), and after the two-sided
+scaling D^1/2 A D^1/2 the paper also tried (Sec. 2), to the relative residual
 1e-4, 1e-7 and 1e-10 of the GS(2)-scaled system (Sec. 2.2), x0 = 0, at most
 10,000 iterations, Bi-CGSTAB's breakdown threshold 1e-16 * DBL_EPSILON and no
 true-residual restarts (the paper's runs had none).  The ILUT rows of the
@@ -45,21 +46,29 @@ def _systems(which: str, grid4: int):
     raise ValueError(which)
 
 
-def solve_case(g, s, solver: str, scaled: bool, tol: float, m: int = 10, ctx=None):
-    """One solve on the GPU path; returns (converged, iterations, relres, ms)."""
+def solve_case(g, s, solver: str, scaled, tol: float, m: int = 10, ctx=None):
+    """One solve on the GPU path; returns (converged, iterations, relres, ms).
+    scaled: False (original system), True or "gs" (GS(2)), or "sym" (the
+    two-sided D^1/2 A D^1/2 variant of Sec. 2, stopping on the GS(2)-scaled
+    residual of the original system; x = D^1/2 y is formed afterwards)."""
     import torch
 
     A = g.Csr.from_host(s.rowptr, s.colidx, s.val, device="cuda")
     b = torch.as_tensor(s.b, device="cuda")
-    if scaled:
+    w = sv = None
+    if scaled == "sym":
+        sv, w = g.gs_scale_sym(A, b, p=2.0, weights=True, ctx=ctx)
+    elif scaled:
         g.gs_scale(A, b, p=2.0, ctx=ctx)
     x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
-    o = g.opts(maxit=MAXIT, refresh=0)
+    o = g.opts(maxit=MAXIT, refresh=0, weights=w)
     t0 = time.perf_counter()
     if solver == "gmres":
         info = g.gmres_solve(A, b, x, m=m, tol=tol, options=o, ctx=ctx)
     else:
         info = g.bicgstab_solve(A, b, x, tol=tol, options=o, ctx=ctx)
+    if sv is not None:
+        g.diag_mul(sv, x, ctx=ctx)
     torch.cuda.synchronize()
     ms = 1e3 * (time.perf_counter() - t0)
     return info["conv"] == 0, int(info["iters"]), float(info["relres_true"]), ms
@@ -75,13 +84,14 @@ def run(tables, grid4: int = 80, out=print):
             out("| method | rel-res 1e-4 | rel-res 1e-7 | rel-res 1e-10 |")
             out("|---|---|---|---|")
             for solver in ("bicgstab", "gmres"):
-                for scaled in (False, True):
+                for scaled in (False, True, "sym"):
                     cells = []
                     for tol in TOLS:
                         conv, it, rr, ms = solve_case(g, s, solver, scaled, tol)
                         results[(t, label, solver, scaled, tol)] = (conv, it, rr, ms)
                         cells.append(f"{it} ({ms / 1e3:.2f} s)" if conv else f"no conv. ({rr:.1e})")
-                    name = ("Bi-CGSTAB" if solver == "bicgstab" else "GMRES(10)") + (" with GS(2)" if scaled else "")
+                    name = ("Bi-CGSTAB" if solver == "bicgstab" else "GMRES(10)") + (
+                        " with D^1/2 A D^1/2" if scaled == "sym" else (" with GS(2)" if scaled else ""))
                     out(f"| {name} | " + " | ".join(cells) + " |")
     return results
 
