@@ -50,9 +50,12 @@ def lib():
         L.or_metric_weights.argtypes = [C.c_int, _ip, _dp, _dp]
         L.or_arnoldi.argtypes = [C.c_int, _ip, _ip, _dp, _dp, C.c_int, _dp, _dp]
         L.or_gmres.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_int, C.c_double,
-                               C.c_int, vp, C.POINTER(_Info), vp]
+                               C.c_int, vp, vp, C.POINTER(_Info), vp]
         L.or_bicgstab.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_double, C.c_int,
-                                  C.c_int, vp, C.POINTER(_Info), vp]
+                                  C.c_int, vp, vp, C.POINTER(_Info), vp]
+        L.or_ilu0.argtypes = [C.c_int, _ip, _ip, _dp, _dp]
+        L.or_ilu0_apply.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp]
+        L.or_ilu0_apply.restype = None
         _lib = L
     return _lib
 
@@ -123,8 +126,27 @@ def arnoldi(rowptr, colidx, val, v0, k):
     return V.reshape(k + 1, n).T, H.reshape(k, k + 1).T, steps
 
 
-def gmres(rowptr, colidx, val, b, m=30, tol=1e-8, maxit=10000, x0=None, w=None, history=False):
-    """Restarted GMRES(m) with CGS2; returns (x, info dict[, history])."""
+def ilu0(rowptr, colidx, val):
+    """ILU(0) factors (Saad Alg. 10.4) on A's pattern: L unit lower and U
+    stored together in A's layout."""
+    rowptr, colidx, val = _csr(rowptr, colidx, val)
+    lu = np.empty_like(val)
+    _check(lib().or_ilu0(len(rowptr) - 1, rowptr, colidx, val, lu))
+    return lu
+
+
+def ilu0_apply(rowptr, colidx, lu, r):
+    """z = (LU)^-1 r."""
+    rowptr, colidx, lu = _csr(rowptr, colidx, lu)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    z = np.empty_like(r)
+    lib().or_ilu0_apply(len(r), rowptr, colidx, lu, r, z)
+    return z
+
+
+def gmres(rowptr, colidx, val, b, m=30, tol=1e-8, maxit=10000, x0=None, w=None, history=False, lu=None):
+    """Restarted GMRES(m) with CGS2, right-preconditioned by ILU(0) factors
+    lu when given; returns (x, info dict[, history])."""
     rowptr, colidx, val = _csr(rowptr, colidx, val)
     n = len(rowptr) - 1
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -132,16 +154,18 @@ def gmres(rowptr, colidx, val, b, m=30, tol=1e-8, maxit=10000, x0=None, w=None, 
     ww = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
     hist = np.full(maxit, np.nan) if history else None
     info = _Info()
+    lu = None if lu is None else np.ascontiguousarray(lu, dtype=np.float64)
     _check(lib().or_gmres(n, rowptr, colidx, val, b, x, int(m), float(tol), int(maxit),
-                          _ptr(ww), C.byref(info), _ptr(hist)))
+                          _ptr(ww), _ptr(lu), C.byref(info), _ptr(hist)))
     d = info.as_dict()
     if history:
         return x, d, hist[: d["iters"]]
     return x, d
 
 
-def bicgstab(rowptr, colidx, val, b, tol=1e-8, maxit=10000, refresh=3, x0=None, w=None, history=False):
-    """Bi-CGSTAB with true-residual confirmation; returns (x, info dict[, history])."""
+def bicgstab(rowptr, colidx, val, b, tol=1e-8, maxit=10000, refresh=3, x0=None, w=None, history=False, lu=None):
+    """Bi-CGSTAB with true-residual confirmation, right-preconditioned by
+    ILU(0) factors lu when given; returns (x, info dict[, history])."""
     rowptr, colidx, val = _csr(rowptr, colidx, val)
     n = len(rowptr) - 1
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -149,8 +173,9 @@ def bicgstab(rowptr, colidx, val, b, tol=1e-8, maxit=10000, refresh=3, x0=None, 
     ww = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
     hist = np.full(maxit, np.nan) if history else None
     info = _Info()
+    lu = None if lu is None else np.ascontiguousarray(lu, dtype=np.float64)
     _check(lib().or_bicgstab(n, rowptr, colidx, val, b, x, float(tol), int(maxit), int(refresh),
-                             _ptr(ww), C.byref(info), _ptr(hist)))
+                             _ptr(ww), _ptr(lu), C.byref(info), _ptr(hist)))
     d = info.as_dict()
     if history:
         return x, d, hist[: d["iters"]]

@@ -18,6 +18,8 @@
  *              problem.
  *   Bi-CGSTAB  Sec. 2 and 2.2 (van der Vorst 1992); breakdown tolerance
  *              1e-16 * DBL_EPSILON relative to the vector norms (Sec. 2.2).
+ *   ILU(0)     Sec. 2 (ILUT with drop tolerance 0 and fill-in 1 behaves as
+ *              ILU(0)); Saad's IKJ algorithm; right preconditioning.
  *   Stopping   Sec. 2.2: ||b - Ax|| / ||b - Ax0|| < eps measured on the
  *              GS(2)-scaled system, i.e. with weights w_i = 1/||a_i||_2 of the
  *              matrix being solved; 10,000-iteration cap; x0 = 0 (Sec. 2.1).
@@ -183,10 +185,84 @@ int or_metric_weights(int n, const int* rowptr, const double* val, double* w) {
  * w = A v_j, h1 = V^T w, w -= V h1, h2 = V^T w, w -= V h2, and returns in
  * hcol[0..j] the sum h1 + h2 and in hcol[j+1] = ||w||.  w is left in wout.
  * *aw_norm receives ||A v_j|| (used by the breakdown test). */
-static void arnoldi_step(int n, const int* rp, const int* ci, const double* va,
+/* ------------------------------------------------------------ ILU(0) */
+
+/* ILU(0) (Sec. 2: the paper's ILUT with drop tolerance 0 and fill-in 1 acted
+ * as ILU(0)), in the IKJ form of Saad, Iterative Methods for Sparse Linear
+ * Systems, Alg. 10.4: L (unit lower) and U share A's sparsity pattern and
+ * are stored together in lu (A's layout).  For each row i and each k < i in
+ * its pattern, in column order: l_ik = a_ik / u_kk, then a_ij -= l_ik u_kj
+ * for every j > k present in both rows i and k.
+ * Rows must hold their diagonal and sorted column indices; a zero pivot is an
+ * error. */
+int or_ilu0(int n, const int* rp, const int* ci, const double* va, double* lu) {
+  if (n <= 0) return OR_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    int has_diag = 0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      if (ci[k] < 0 || ci[k] >= n) return OR_ERR_ARG;
+      if (k > rp[i] && ci[k] <= ci[k - 1]) return OR_ERR_ARG;
+      if (ci[k] == i) has_diag = 1;
+      lu[k] = va[k];
+    }
+    if (!has_diag) return OR_ERR_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    for (int kk = rp[i]; kk < rp[i + 1] && ci[kk] < i; ++kk) {
+      const int k = ci[kk];
+      double ukk = 0.0;
+      for (int q = rp[k]; q < rp[k + 1]; ++q)
+        if (ci[q] == k) ukk = lu[q];
+      if (ukk == 0.0) return OR_ERR_ZERO_ROW;
+      lu[kk] = lu[kk] / ukk;
+      for (int jj = kk + 1; jj < rp[i + 1]; ++jj) {
+        const int j = ci[jj];
+        for (int q = rp[k]; q < rp[k + 1]; ++q)
+          if (ci[q] == j) lu[jj] -= lu[kk] * lu[q];
+      }
+    }
+    double uii = 0.0;
+    for (int q = rp[i]; q < rp[i + 1]; ++q)
+      if (ci[q] == i) uii = lu[q];
+    if (uii == 0.0 || !isfinite(uii)) return OR_ERR_ZERO_ROW;
+  }
+  return OR_OK;
+}
+
+/* z = (LU)^-1 r: forward substitution with the unit lower factor, then
+ * backward substitution with the upper factor, rows in order. */
+void or_ilu0_apply(int n, const int* rp, const int* ci, const double* lu, const double* r, double* z) {
+  for (int i = 0; i < n; ++i) {
+    double s = r[i];
+    for (int k = rp[i]; k < rp[i + 1] && ci[k] < i; ++k) s -= lu[k] * z[ci[k]];
+    z[i] = s;
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = z[i], d = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      if (ci[k] > i) s -= lu[k] * z[ci[k]];
+      else if (ci[k] == i) d = lu[k];
+    }
+    z[i] = s / d;
+  }
+}
+
+/* y = A M^-1 x with M = LU from or_ilu0 (right preconditioning), or y = A x
+ * when lu is NULL; tmp is scratch [n]. */
+static void precond_spmv(int n, const int* rp, const int* ci, const double* va, const double* lu,
+                         const double* x, double* y, double* tmp) {
+  if (lu) {
+    or_ilu0_apply(n, rp, ci, lu, x, tmp);
+    or_spmv(n, rp, ci, va, tmp, y);
+  } else {
+    or_spmv(n, rp, ci, va, x, y);
+  }
+}
+
+static void arnoldi_step(int n, const int* rp, const int* ci, const double* va, const double* lu,
                          const double* V, int j, double* hcol, double* wout,
-                         double* h2, double* aw_norm) {
-  or_spmv(n, rp, ci, va, V + (size_t)j * n, wout);
+                         double* h2, double* aw_norm, double* tmp) {
+  precond_spmv(n, rp, ci, va, lu, V + (size_t)j * n, wout, tmp);
   *aw_norm = sqrt(dot(n, wout, wout));
   for (int k = 0; k <= j; ++k) hcol[k] = dot(n, V + (size_t)k * n, wout);
   for (int k = 0; k <= j; ++k) {
@@ -217,7 +293,7 @@ int or_arnoldi(int n, const int* rp, const int* ci, const double* va,
     double awn;
     double* hcol = H + (size_t)j * (k + 1);
     double* w = V + (size_t)(j + 1) * n;
-    arnoldi_step(n, rp, ci, va, V, j, hcol, w, h2, &awn);
+    arnoldi_step(n, rp, ci, va, NULL, V, j, hcol, w, h2, &awn, NULL);
     done = j + 1;
     if (hcol[j + 1] == 0.0) break;
     for (int i = 0; i < n; ++i) w[i] /= hcol[j + 1];
@@ -242,7 +318,7 @@ int or_arnoldi(int n, const int* rp, const int* ci, const double* va,
  * hist (optional, length maxit) receives |g_j+1| / ||r0|| per step. */
 int or_gmres(int n, const int* rp, const int* ci, const double* va,
              const double* b, double* x, int m, double tol, int maxit,
-             const double* w_in, or_info* info, double* hist) {
+             const double* w_in, const double* lu, or_info* info, double* hist) {
   memset(info, 0, sizeof(*info));
   if (n <= 0 || m < 1 || maxit < 0 || !(tol >= 0.0)) return OR_ERR_ARG;
   size_t nn = (size_t)n;
@@ -255,13 +331,15 @@ int or_gmres(int n, const int* rp, const int* ci, const double* va,
   double* h2 = (double*)calloc(m + 1, sizeof(double));
   double* r = (double*)malloc(sizeof(double) * nn);
   double* wv = (double*)malloc(sizeof(double) * nn);
-  if (!V || !H || !g || !cs || !sn || !y || !h2 || !r || !wv) {
-    free(V); free(H); free(g); free(cs); free(sn); free(y); free(h2); free(r); free(wv);
+  double* tmp = (double*)malloc(sizeof(double) * nn);
+  double* u = (double*)malloc(sizeof(double) * nn);
+  if (!V || !H || !g || !cs || !sn || !y || !h2 || !r || !wv || !tmp || !u) {
+    free(V); free(H); free(g); free(cs); free(sn); free(y); free(h2); free(r); free(wv); free(tmp); free(u);
     return OR_ERR_OOM;
   }
   const double* w = w_in;
   if (!w) {
-    if (or_metric_weights(n, rp, va, wv) != OR_OK) { free(V); free(H); free(g); free(cs); free(sn); free(y); free(h2); free(r); free(wv); return OR_ERR_ZERO_ROW; }
+    if (or_metric_weights(n, rp, va, wv) != OR_OK) { free(V); free(H); free(g); free(cs); free(sn); free(y); free(h2); free(r); free(wv); free(tmp); free(u); return OR_ERR_ZERO_ROW; }
     w = wv;
   }
 
@@ -285,7 +363,7 @@ int or_gmres(int n, const int* rp, const int* ci, const double* va,
       double* hcol = H + (size_t)j * (m + 1);
       double* wj = V + (size_t)(j + 1) * nn;
       double awn;
-      arnoldi_step(n, rp, ci, va, V, j, hcol, wj, h2, &awn);
+      arnoldi_step(n, rp, ci, va, lu, V, j, hcol, wj, h2, &awn, tmp);
       info->iters++;
       kcols = j + 1;
       double hnext = hcol[j + 1];
@@ -315,9 +393,19 @@ int or_gmres(int n, const int* rp, const int* ci, const double* va,
       for (int k = i + 1; k < kcols; ++k) s -= H[(size_t)k * (m + 1) + i] * y[k];
       y[i] = s / H[(size_t)i * (m + 1) + i];
     }
-    for (int k = 0; k < kcols; ++k) {
-      const double* vk = V + (size_t)k * nn;
-      for (size_t i = 0; i < nn; ++i) x[i] += y[k] * vk[i];
+    if (lu) { /* x += M^-1 (V y) */
+      for (size_t i = 0; i < nn; ++i) u[i] = 0.0;
+      for (int k = 0; k < kcols; ++k) {
+        const double* vk = V + (size_t)k * nn;
+        for (size_t i = 0; i < nn; ++i) u[i] += y[k] * vk[i];
+      }
+      or_ilu0_apply(n, rp, ci, lu, u, tmp);
+      for (size_t i = 0; i < nn; ++i) x[i] += tmp[i];
+    } else { /* x += V y */
+      for (int k = 0; k < kcols; ++k) {
+        const double* vk = V + (size_t)k * nn;
+        for (size_t i = 0; i < nn; ++i) x[i] += y[k] * vk[i];
+      }
     }
     residual(n, rp, ci, va, b, x, r);
     double mu = wnorm(n, w, r) / mu0;
@@ -330,7 +418,7 @@ int or_gmres(int n, const int* rp, const int* ci, const double* va,
   }
 out:
   if (info->conv == OR_CONVERGED && info->iters == 0) info->relres_true = 0.0;
-  free(V); free(H); free(g); free(cs); free(sn); free(y); free(h2); free(r); free(wv);
+  free(V); free(H); free(g); free(cs); free(sn); free(y); free(h2); free(r); free(wv); free(tmp); free(u);
   return OR_OK;
 }
 
@@ -355,7 +443,7 @@ out:
  * hist (optional, length maxit) receives the recursive metric per iteration. */
 int or_bicgstab(int n, const int* rp, const int* ci, const double* va,
                 const double* b, double* x, double tol, int maxit, int refresh,
-                const double* w_in, or_info* info, double* hist) {
+                const double* w_in, const double* lu, or_info* info, double* hist) {
   memset(info, 0, sizeof(*info));
   if (n <= 0 || maxit < 0 || !(tol >= 0.0) || refresh < 0) return OR_ERR_ARG;
   size_t nn = (size_t)n;
@@ -366,14 +454,21 @@ int or_bicgstab(int n, const int* rp, const int* ci, const double* va,
   double* s = (double*)malloc(sizeof(double) * nn);
   double* t = (double*)malloc(sizeof(double) * nn);
   double* wv = (double*)malloc(sizeof(double) * nn);
-  if (!r || !rh || !p || !v || !s || !t || !wv) {
-    free(r); free(rh); free(p); free(v); free(s); free(t); free(wv);
+  double* ph = (double*)malloc(sizeof(double) * nn); /* M^-1 p */
+  double* sh = (double*)malloc(sizeof(double) * nn); /* M^-1 s */
+  if (!r || !rh || !p || !v || !s || !t || !wv || !ph || !sh) {
+    free(r); free(rh); free(p); free(v); free(s); free(t); free(wv); free(ph); free(sh);
     return OR_ERR_OOM;
   }
+  /* with a preconditioner M = LU (right preconditioning) the products are
+   * A M^-1 p and A M^-1 s, and x moves along M^-1 p and M^-1 s; without one
+   * ph and sh are p and s themselves */
+  const double* pp = lu ? ph : p;
+  const double* ss = lu ? sh : s;
   const double brk = 1e-16 * DBL_EPSILON;
   const double* w = w_in;
   if (!w) {
-    if (or_metric_weights(n, rp, va, wv) != OR_OK) { free(r); free(rh); free(p); free(v); free(s); free(t); free(wv); return OR_ERR_ZERO_ROW; }
+    if (or_metric_weights(n, rp, va, wv) != OR_OK) { free(r); free(rh); free(p); free(v); free(s); free(t); free(wv); free(ph); free(sh); return OR_ERR_ZERO_ROW; }
     w = wv;
   }
   residual(n, rp, ci, va, b, x, r);
@@ -389,7 +484,8 @@ int or_bicgstab(int n, const int* rp, const int* ci, const double* va,
     int check_true = 0;
     while (!check_true) {
       if (info->iters >= maxit) { info->conv = OR_MAXIT; goto final; }
-      or_spmv(n, rp, ci, va, p, v);
+      if (lu) or_ilu0_apply(n, rp, ci, lu, p, ph);
+      or_spmv(n, rp, ci, va, pp, v);
       double sigma = dot(n, rh, v);
       double vn = sqrt(dot(n, v, v));
       if (fabs(sigma) <= brk * rhn * vn) { info->conv = OR_BREAKDOWN; goto final; }
@@ -397,19 +493,20 @@ int or_bicgstab(int n, const int* rp, const int* ci, const double* va,
       for (size_t i = 0; i < nn; ++i) s[i] = r[i] - alpha * v[i];
       double mus = wnorm(n, w, s) / mu0;
       if (mus < tol) {
-        for (size_t i = 0; i < nn; ++i) x[i] += alpha * p[i];
+        for (size_t i = 0; i < nn; ++i) x[i] += alpha * pp[i];
         info->iters++;
         info->relres_rec = mus;
         if (hist) hist[info->iters - 1] = mus;
         check_true = 1;
         break;
       }
-      or_spmv(n, rp, ci, va, s, t);
+      if (lu) or_ilu0_apply(n, rp, ci, lu, s, sh);
+      or_spmv(n, rp, ci, va, ss, t);
       double tt = dot(n, t, t);
       double ts = dot(n, t, s);
       if (tt == 0.0) { info->conv = OR_BREAKDOWN; goto final; }
       double omega = ts / tt;
-      for (size_t i = 0; i < nn; ++i) x[i] += alpha * p[i] + omega * s[i];
+      for (size_t i = 0; i < nn; ++i) x[i] += alpha * pp[i] + omega * ss[i];
       for (size_t i = 0; i < nn; ++i) r[i] = s[i] - omega * t[i];
       info->iters++;
       double mur = wnorm(n, w, r) / mu0;
@@ -437,6 +534,6 @@ final:
   residual(n, rp, ci, va, b, x, t);
   info->relres_true = wnorm(n, w, t) / mu0;
 out:
-  free(r); free(rh); free(p); free(v); free(s); free(t); free(wv);
+  free(r); free(rh); free(p); free(v); free(s); free(t); free(wv); free(ph); free(sh);
   return OR_OK;
 }

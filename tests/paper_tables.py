@@ -29,7 +29,7 @@ def load(path: str = FIXTURE) -> list[dict]:
             continue
         t = ln.split()
         rows.append({"table": t[0], "case": t[1], "solver": t[2], "m": None if t[3] == "-" else int(t[3]),
-                     "scaling": t[4], "entries": dict(zip(TOLS, (_entry(x) for x in t[5:8])))})
+                     "scaling": t[4], "precond": t[5], "entries": dict(zip(TOLS, (_entry(x) for x in t[6:9])))})
     return rows
 
 

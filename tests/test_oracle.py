@@ -190,6 +190,86 @@ def test_sym_scaling_errors():
         oracle.gs_scale_sym(rp, ci, va2, None, 2.0)
 
 
+# ------------------------------------------------------------------ ILU(0)
+def _pattern_dense(rp, ci, v, n):
+    M = np.zeros((n, n))
+    for i in range(n):
+        M[i, ci[rp[i]:rp[i + 1]]] = v[rp[i]:rp[i + 1]]
+    return M
+
+
+def _split_lu(rp, ci, lu, n):
+    F = _pattern_dense(rp, ci, lu, n)
+    return np.tril(F, -1) + np.eye(n), np.triu(F)
+
+
+def test_ilu0_is_exact_lu_on_a_tridiagonal_matrix():
+    """No fill-in arises for a tridiagonal matrix, so ILU(0) = LU: the
+    preconditioned system is the identity and GMRES needs one step."""
+    n = 50
+    rs = np.random.default_rng(5)
+    T = np.diag(rs.uniform(3, 4, n)) + np.diag(rs.uniform(-1, 1, n - 1), 1) + np.diag(rs.uniform(-1, 1, n - 1), -1)
+    rp = np.zeros(n + 1, dtype=np.int32)
+    cols, vals = [], []
+    for i in range(n):
+        nz = np.nonzero(T[i])[0]
+        cols.extend(nz)
+        vals.extend(T[i, nz])
+        rp[i + 1] = len(cols)
+    ci, va = np.array(cols, dtype=np.int32), np.array(vals)
+    lu = oracle.ilu0(rp, ci, va)
+    L, U = _split_lu(rp, ci, lu, n)
+    assert np.allclose(L @ U, T, rtol=0, atol=1e-14)
+    b = rs.normal(size=n)
+    x, info = oracle.gmres(rp, ci, va, b, m=10, tol=1e-12, lu=lu)
+    assert info["iters"] == 1 and info["conv"] == 0
+    assert np.allclose(T @ x, b, atol=1e-12)
+
+
+def test_ilu0_matches_a_on_its_pattern():
+    """The defining property of ILU(0): (LU)_ij = a_ij wherever a_ij is in
+    the pattern (the fill-in outside it is what is dropped)."""
+    s = configs.c1(9)
+    lu = oracle.ilu0(s.rowptr, s.colidx, s.val)
+    L, U = _split_lu(s.rowptr, s.colidx, lu, s.n)
+    A = s.dense()
+    mask = _pattern_dense(s.rowptr, s.colidx, np.ones_like(s.val), s.n) != 0
+    assert np.allclose((L @ U)[mask], A[mask], rtol=1e-13, atol=1e-12)
+    assert np.abs((L @ U)[~mask]).max() > 1e-3  # fill-in was dropped
+    r = np.random.default_rng(6).normal(size=s.n)
+    z = oracle.ilu0_apply(s.rowptr, s.colidx, lu, r)
+    assert np.allclose(L @ (U @ z), r, rtol=1e-12, atol=1e-12)
+
+
+def test_ilu0_is_row_scaling_equivariant():
+    """For a positive diagonal D, ILU(0)(DA) = (D L D^-1, D U): the GS-scaled
+    system's preconditioned operator is similar to the original one."""
+    s = configs.c1(8)
+    d = np.random.default_rng(7).uniform(0.5, 3.0, s.n)
+    rows = np.repeat(np.arange(s.n), np.diff(s.rowptr))
+    lu1 = oracle.ilu0(s.rowptr, s.colidx, s.val)
+    lu2 = oracle.ilu0(s.rowptr, s.colidx, s.val * d[rows])
+    L1, U1 = _split_lu(s.rowptr, s.colidx, lu1, s.n)
+    L2, U2 = _split_lu(s.rowptr, s.colidx, lu2, s.n)
+    assert np.allclose(L2, np.diag(d) @ L1 @ np.diag(1 / d), rtol=1e-12, atol=1e-14)
+    assert np.allclose(U2, np.diag(d) @ U1, rtol=1e-12, atol=1e-14)
+
+
+def test_ilu0_errors():
+    s = configs.c1(6)
+    nodiag_rp = s.rowptr.copy()
+    with pytest.raises(oracle.OracleError):  # no diagonal entry in row 0
+        keep = np.ones(len(s.colidx), dtype=bool)
+        keep[np.nonzero(s.colidx[s.rowptr[0]:s.rowptr[1]] == 0)[0][0]] = False
+        rp = np.concatenate([[0], np.cumsum([np.count_nonzero(keep[s.rowptr[i]:s.rowptr[i + 1]])
+                                             for i in range(s.n)])]).astype(np.int32)
+        oracle.ilu0(rp, s.colidx[keep], s.val[keep])
+    bad = s.colidx.copy()
+    bad[0], bad[1] = bad[1], bad[0]  # unsorted row
+    with pytest.raises(oracle.OracleError):
+        oracle.ilu0(nodiag_rp, bad, s.val)
+
+
 # ------------------------------------------------------------------ SpMV
 def test_spmv_matches_dense():
     A, rp, ci, va = _random_csr(37, 3)

@@ -2,7 +2,8 @@
 (Sec. 3, Tables 1 and 1a; fixture tests/golden/table1_p1_iterations.txt):
 128x128 grid, b = A (1,...,1)^T, x0 = 0, maxit 10,000, the GS(2)-scaled
 relative residual as the stopping metric, GMRES(10) and Bi-CGSTAB without
-and with GS(2).
+and with GS(2), without a preconditioner and with ILU(0) (the paper's
+ILUT(0, fill-in 1), which it found to act as ILU(0)).
 
 These pin the oracle's whole solve (discretisation of Problem 1, GS,
 GMRES(m) with CGS2, Bi-CGSTAB, the stopping rule) to numbers the paper
@@ -37,12 +38,21 @@ def _scaled(case, scaling):
     return _CACHE[key]
 
 
+_LU = {}
+
+
 def _run(row, tol):
     s, val, b = _scaled(row["case"], row["scaling"])
+    lu = None
+    if row.get("precond", "none") == "ilut":  # ILUT(0, fill 1) acts as ILU(0), Sec. 2
+        key = (row["case"], row["scaling"])
+        if key not in _LU:
+            _LU[key] = oracle.ilu0(s.rowptr, s.colidx, val)
+        lu = _LU[key]
     if row["solver"] == "gmres":
-        _, info = oracle.gmres(s.rowptr, s.colidx, val, b, m=row["m"], tol=tol, maxit=10000)
+        _, info = oracle.gmres(s.rowptr, s.colidx, val, b, m=row["m"], tol=tol, maxit=10000, lu=lu)
     else:
-        _, info = oracle.bicgstab(s.rowptr, s.colidx, val, b, tol=tol, maxit=10000, refresh=0)
+        _, info = oracle.bicgstab(s.rowptr, s.colidx, val, b, tol=tol, maxit=10000, refresh=0, lu=lu)
     return info
 
 
@@ -58,7 +68,8 @@ def _cases():
                 if done_stag:
                     continue
                 done_stag = True
-            out.append(pytest.param(r, tol, id=f"{r['table']}-{r['case']}-{r['solver']}-{r['scaling']}-{tol:g}"))
+            out.append(pytest.param(r, tol, id=f"{r['table']}-{r['case']}-{r['solver']}-{r['scaling']}-"
+                                              f"{r['precond']}-{tol:g}"))
     return out
 
 
