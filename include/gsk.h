@@ -78,6 +78,9 @@ typedef struct {
   int32_t dtype;         /* gsk_dtype */
 } gsk_csr;
 
+/* ILU(0) factors of a matrix on the device (gsk_ilu0_create). */
+typedef struct gsk_ilu0 gsk_ilu0;
+
 /* Solver options; gsk_opts_default() fills the paper's settings. */
 typedef struct {
   int32_t maxit;          /* iteration cap, default 10000 (Sec. 2.2) */
@@ -96,6 +99,11 @@ typedef struct {
                              (for GMRES one step is one inner cycle); 0, the
                              default, means no cap beyond maxit, which always
                              bounds the total inner iterations */
+  const gsk_ilu0* precond;/* optional ILU(0) preconditioner of the matrix being
+                             solved, applied on the right (x = M^-1 u), so the
+                             residual and the stopping metric stay those of
+                             A x = b; NULL (the default) = none.  FP64 solvers
+                             only (GSK_ERR_ARG with GSK_PREC_MIXED) */
 } gsk_opts;
 
 /* Result of a solve (host memory). */
@@ -192,6 +200,36 @@ gsk_status gs_scale_sym(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* s_o
  * y into x = D^(1/2) y (Sec. 2).  Asynchronous on `stream`.
  */
 gsk_status gsk_diag_mul(gsk_ctx* ctx, int n, const double* s, void* x, gsk_dtype dtype, void* stream);
+
+/*
+ * gsk_ilu0_create -- ILU(0) factors of A for right preconditioning (Sec. 2:
+ * the paper's ILUT with drop tolerance 0 and fill-in 1 acted as ILU(0)).
+ * L (unit lower) and U have A's sparsity pattern (Saad's IKJ form: for each
+ * row i and k < i in its pattern, l_ik = a_ik / u_kk, then a_ij -= l_ik u_kj
+ * for the j > k present in both rows).  The rows are processed by level sets
+ * of their dependency graph, computed on the host from A's structure (one
+ * copy of rowptr and colidx to the host); the factorisation and every later
+ * application run on the device, one cooperative launch each.
+ *   A    FP64, every row holding its diagonal, columns sorted within a row.
+ *        The handle keeps A's rowptr and colidx pointers: they must stay
+ *        valid and unchanged while the handle is used (its values are
+ *        copied).
+ *   out  receives the handle (owns device memory; free with gsk_ilu0_destroy)
+ * Errors: GSK_ERR_ARG (FP32 matrix, missing diagonal, unsorted or
+ * out-of-range columns), GSK_ERR_ZERO_ROW (a zero pivot), GSK_ERR_OOM,
+ * GSK_ERR_CUDA; GSK_ERR_TIMEOUT if a bounded wait between levels gave up.
+ * Synchronises `stream`.  One solve at a time may use a handle.
+ */
+gsk_status gsk_ilu0_create(gsk_ctx* ctx, const gsk_csr* A, gsk_ilu0** out, void* stream);
+gsk_status gsk_ilu0_destroy(gsk_ilu0* ilu);
+
+/*
+ * gsk_ilu0_apply -- z = (LU)^-1 r: forward substitution with L, backward with
+ * U, by level sets.  r, z: device FP64 [n], distinct.  Asynchronous on
+ * `stream`; a timed-out wait is reported by the next gsk_ilu0_create or by
+ * the solve that uses the handle.
+ */
+gsk_status gsk_ilu0_apply(gsk_ctx* ctx, const gsk_ilu0* ilu, const double* r, double* z, void* stream);
 
 /*
  * gsk_spmv -- y = A x, the product every Krylov step performs (Sec. 2).

@@ -49,7 +49,7 @@ class CsrC(C.Structure):
 class OptsC(C.Structure):
     _fields_ = [("maxit", C.c_int32), ("refresh", C.c_int32), ("precision", C.c_int32), ("metric", C.c_int32),
                 ("weights", C.c_void_p), ("inner_tol", C.c_double), ("inner_maxit", C.c_int32),
-                ("max_refinements", C.c_int32)]
+                ("max_refinements", C.c_int32), ("precond", C.c_void_p)]
 
 
 class InfoC(C.Structure):
@@ -81,6 +81,9 @@ SIGNATURES = {
     "gs_scale_sym": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p],
                      C.c_int),
     "gsk_diag_mul": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "gsk_ilu0_create": ([C.c_void_p, C.POINTER(CsrC), C.POINTER(C.c_void_p), C.c_void_p], C.c_int),
+    "gsk_ilu0_destroy": ([C.c_void_p], C.c_int),
+    "gsk_ilu0_apply": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gsk_spmv": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gmres_solve": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                      C.POINTER(OptsC), C.POINTER(InfoC), C.c_void_p], C.c_int),
@@ -213,13 +216,51 @@ def _ptr(t):
 
 
 def opts(maxit=10000, refresh=3, precision=PREC_F64, metric=METRIC_GS2, weights=None, inner_tol=1e-5,
-         inner_maxit=0, max_refinements=0) -> OptsC:
+         inner_maxit=0, max_refinements=0, precond=None) -> OptsC:
+    """Solver options; precond: an Ilu0 of the matrix being solved (applied on
+    the right), or None."""
     o = OptsC()
     lib().gsk_opts_default(C.byref(o))
     o.maxit, o.refresh, o.precision, o.metric = maxit, refresh, precision, metric
     o.weights = None if weights is None else weights.data_ptr()
     o.inner_tol, o.inner_maxit, o.max_refinements = inner_tol, inner_maxit, max_refinements
+    o.precond = None if precond is None else precond.handle
     return o
+
+
+class Ilu0:
+    """ILU(0) factors of a device CSR matrix (FP64, diagonal present, sorted
+    columns), computed on the device by gsk_ilu0_create; use as
+    opts(precond=...) or apply z = (LU)^-1 r with apply().  Keeps a reference
+    to the matrix, whose structure the factors share."""
+
+    def __init__(self, A: Csr, ctx: Context | None = None, stream=None):
+        self.ctx = ctx or default_context(A.val.device.index or 0)
+        self.A = A
+        self._h = C.c_void_p()
+        Ac = A.c()
+        self.ctx.check(lib().gsk_ilu0_create(self.ctx.handle, C.byref(Ac), C.byref(self._h), _stream_ptr(stream)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def apply(self, r, z=None, stream=None):
+        if z is None:
+            z = _torch().empty_like(r)
+        self.ctx.check(lib().gsk_ilu0_apply(self.ctx.handle, self._h, _ptr(r), _ptr(z), _stream_ptr(stream)))
+        return z
+
+    def close(self):
+        if self._h:
+            lib().gsk_ilu0_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # interpreter shutdown
+            pass
 
 
 def gs_scale(A: Csr, b=None, p: float = 2.0, d_out=None, ctx: Context | None = None, stream=None):

@@ -475,6 +475,7 @@ extern "C" gsk_status bicgstab_solve_batched(gsk_ctx* ctx, int nsys, const gsk_c
   if (!(tol >= 0.0) || opts.maxit < 0 || opts.refresh < 0 || !(opts.inner_tol > 0.0) || opts.inner_maxit < 0)
     return ctx->fail(GSK_ERR_ARG, "bad tol/maxit/refresh/inner_tol");
   if (opts.weights) return ctx->fail(GSK_ERR_ARG, "the batched solver derives its metric weights itself");
+  if (opts.precond) return ctx->fail(GSK_ERR_ARG, "the batched solver takes no preconditioner");
   if (nsys == 0) return GSK_OK;
   const bool mixed = opts.precision == GSK_PREC_MIXED;
   std::vector<BatchSys> hs(nsys);

@@ -2,6 +2,7 @@
 // point and the stream-mode profiler.  The kernels are in bicgstab_kernels.cuh.
 #include "bicgstab_kernels.cuh"
 #include "graph.hpp"
+#include "ilu.cuh"
 
 namespace gsk {
 
@@ -10,10 +11,16 @@ namespace gsk {
 // Bi-CGSTAB iterations per pass of the graph's loop body.
 constexpr int kBcgUnroll = 4;
 
+// launches that apply the right preconditioner M (ILU(0)): p^ = M^-1 p before
+// the product A p^, s^ = M^-1 s before A s^
+constexpr int kBcgIluP = 1000, kBcgIluS = 1001;
+
 struct BcgPlan {
   int g_tile, g_k2a, g_k3, g_k4, wmode;
   BcgArgs<double> a;
   double* wbuf;  // weights computed by the solver (or nullptr)
+  const gsk_ilu0* pre = nullptr;
+  double *ph = nullptr, *sh = nullptr;  // M^-1 p, M^-1 s
   BcgState host_state;
 };
 
@@ -26,7 +33,20 @@ static void bcg_launch(gsk_ctx* ctx, BcgPlan& P, int k, cudaStream_t s) {
     case kKBcgK1: bcg_k1<double><<<P.g_tile, kBlock, 0, s>>>(a); break;
     case kKBcgK2a: bcg_k2a<double><<<P.g_k2a, kBlock, 0, s>>>(a); break;
     case kKBcgK2b: bcg_k2b<double><<<P.g_tile, kBlock, 0, s>>>(a); break;
-    case kKBcgK3: bcg_k3<double><<<P.g_k3, kBlock, 0, s>>>(a); break;
+    case kKBcgK3:
+      if (P.pre) bcg_k3<double, true><<<P.g_k3, kBlock, 0, s>>>(a);
+      else bcg_k3<double, false><<<P.g_k3, kBlock, 0, s>>>(a);
+      break;
+    case kBcgIluP:
+    case kBcgIluS: {
+      IluGate g = {};
+      g.base = k == kBcgIluP ? a.p : a.s;
+      g.skip0 = &a.S->stop;
+      g.skip1 = &a.S->check;
+      g.skip2 = k == kBcgIluS ? &a.S->halfexit : nullptr;
+      ilu_launch_apply(ctx, P.pre, g, k == kBcgIluP ? P.ph : P.sh, s);
+      break;
+    }
     case kKBcgK4: bcg_k4<double><<<P.g_k4, kBlock, 0, s>>>(a); break;
     case kKBcgKt: bcg_kt<double><<<P.g_tile, kBlock, 0, s>>>(a); break;
     case kKBcgKr: bcg_kr<double><<<P.g_k4, kBlock, 0, s>>>(a); break;
@@ -64,8 +84,13 @@ static gsk_status bcg_record(gsk_ctx* ctx, BcgPlan& P, cudaGraphExec_t* exec_out
   // iteration set check or stop; no conditional node inside the body
   Capture c1;
   GSK_CK(c1.begin(cs, wbody));
-  for (int u = 0; u < kBcgUnroll; ++u)
-    for (int k : {kKBcgK1, kKBcgK2a, kKBcgK2b, kKBcgK3, kKBcgK4}) bcg_launch(ctx, P, k, cs);
+  for (int u = 0; u < kBcgUnroll; ++u) {
+    if (P.pre) bcg_launch(ctx, P, kBcgIluP, cs);
+    bcg_launch(ctx, P, kKBcgK1, cs);
+    bcg_launch(ctx, P, kKBcgK2a, cs);
+    if (P.pre) bcg_launch(ctx, P, kBcgIluS, cs);
+    for (int k : {kKBcgK2b, kKBcgK3, kKBcgK4}) bcg_launch(ctx, P, k, cs);
+  }
   bcg_launch(ctx, P, kKBcgKt, cs);
   bcg_launch(ctx, P, kKBcgKr, cs);
   GSK_CK(c1.end());
@@ -81,6 +106,9 @@ static gsk_status bcg_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, voi
   if (!(tol >= 0.0) || opts.maxit < 0 || opts.refresh < 0) return ctx->fail(GSK_ERR_ARG, "bad tol/maxit/refresh");
   if (A->n > 0 && (!b || !x)) return ctx->fail(GSK_ERR_ARG, "NULL b or x");
   const int n = A->n;
+  P.pre = opts.precond;
+  if (P.pre && (P.pre->n != n || P.pre->device != ctx->device))
+    return ctx->fail(GSK_ERR_ARG, "the preconditioner belongs to another matrix or device");
   P.wmode = opts.weights ? 2 : (opts.metric == GSK_METRIC_PLAIN ? 1 : 0);
   P.g_tile = ctx->spmv_grid(n);
   // vector kernels (two FP64 rows per thread): as many blocks as fit, so
@@ -102,6 +130,8 @@ static gsk_status bcg_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, voi
     P.a.s = ar.take<double>(n);
     P.a.t = ar.take<double>(n);
     P.wbuf = P.wmode == 0 ? ar.take<double>(n) : nullptr;
+    P.ph = P.pre ? ar.take<double>(n) : nullptr;
+    P.sh = P.pre ? ar.take<double>(n) : nullptr;
   };
   Arena sizing;
   layout(sizing);
@@ -117,6 +147,8 @@ static gsk_status bcg_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, voi
   P.a.b = (const double*)b;
   P.a.x = (double*)x;
   P.a.w = P.wmode == 0 ? P.wbuf : (P.wmode == 2 ? opts.weights : nullptr);
+  P.a.p_in = P.pre ? P.ph : P.a.p;
+  P.a.s_in = P.pre ? P.sh : P.a.s;
   P.a.in_graph = 0;
   P.a.unrolled = 0;
   P.a.h_while = P.a.h_if = 0;
@@ -205,7 +237,7 @@ extern "C" gsk_status bicgstab_solve(gsk_ctx* ctx, const gsk_csr* A, const void*
   }
   std::vector<uint64_t> key = {1, (uint64_t)A->n, (uint64_t)A->nnz, (uint64_t)A->rowptr, (uint64_t)A->colidx,
                                (uint64_t)A->val, (uint64_t)b, (uint64_t)x, (uint64_t)P.wmode,
-                               (uint64_t)P.a.w, (uint64_t)ctx->ws};
+                               (uint64_t)P.a.w, (uint64_t)ctx->ws, (uint64_t)(P.pre ? P.pre->serial : 0)};
   GraphEntry* ge = ctx->find_graph(key);
   if (!ge) {
     cudaGraphExec_t ex = nullptr;
@@ -223,5 +255,6 @@ extern "C" gsk_status bicgstab_solve(gsk_ctx* ctx, const gsk_csr* A, const void*
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
   *info = gsk_info{out.iters, 0, out.refreshes, 0, out.conv, out.mu_true, out.mu_rec, ms};
+  if (P.pre && (s = ilu_read_err(ctx, P.pre, st)) != GSK_OK) return s;
   return err_bits_status(ctx, bits);
 }

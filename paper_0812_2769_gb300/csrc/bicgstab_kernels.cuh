@@ -45,6 +45,10 @@ struct BcgArgs {
   const T* b;
   T* x;
   T *r, *rh, *p, *v, *s, *t;
+  // the vectors multiplied by A and along which x moves: p and s, or, with a
+  // right preconditioner M, M^-1 p and M^-1 s (Sec. 2)
+  const T* p_in;
+  const T* s_in;
   const double* w;
   BcgState* S;
   GridRed red;
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(kBlock) bcg_k1(BcgArgs<T> a) {
   const T* __restrict__ rh = a.rh;
   T* __restrict__ vout = a.v;
   Acc acc[2] = {Acc(0), Acc(0)};
-  spmv_rows_tma(a.rowptr, a.colidx, a.val, a.p, a.n, a.nnz, pipe, a.err, [&](int i, T v) {
+  spmv_rows_tma(a.rowptr, a.colidx, a.val, a.p_in, a.n, a.nnz, pipe, a.err, [&](int i, T v) {
     vout[i] = v;
     acc[0] = fma((Acc)rh[i], (Acc)v, acc[0]);
     acc[1] = fma((Acc)v, (Acc)v, acc[1]);
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(kBlock) bcg_k2b(BcgArgs<T> a) {
   const T* __restrict__ sv = a.s;
   T* __restrict__ tout = a.t;
   Acc acc[2] = {Acc(0), Acc(0)};
-  spmv_rows_tma(a.rowptr, a.colidx, a.val, a.s, a.n, a.nnz, pipe, a.err, [&](int i, T t) {
+  spmv_rows_tma(a.rowptr, a.colidx, a.val, a.s_in, a.n, a.nnz, pipe, a.err, [&](int i, T t) {
     tout[i] = t;
     acc[0] = fma((Acc)t, (Acc)sv[i], acc[0]);
     acc[1] = fma((Acc)t, (Acc)t, acc[1]);
@@ -239,11 +243,11 @@ __global__ void __launch_bounds__(kBlock) bcg_k2b(BcgArgs<T> a) {
   }
 }
 
-template <bool WID, typename T, typename Acc>
+template <bool WID, bool PRE, typename T, typename Acc>
 __device__ __forceinline__ void bcg_k3_row(const BcgArgs<T>& a, int i, Acc alpha, Acc omega, Acc (&acc)[3]) {
   const Acc s = (Acc)a.s[i];
-  const Acc x = fma(alpha, (Acc)a.p[i], (Acc)a.x[i]);
-  a.x[i] = (T)fma(omega, s, x);
+  const Acc x = fma(alpha, (Acc)a.p_in[i], (Acc)a.x[i]);
+  a.x[i] = (T)fma(omega, PRE ? (Acc)a.s_in[i] : s, x);
   const T r = (T)fma(-omega, (Acc)a.t[i], s);
   a.r[i] = r;
   const Acc rd = (Acc)r;
@@ -257,20 +261,23 @@ __device__ __forceinline__ void bcg_k3_row(const BcgArgs<T>& a, int i, Acc alpha
   }
 }
 
-// x += alpha p + omega s, r = s - omega t, and the sums (r^, r), ||W r||^2
-// and (weights present) ||r||^2; WID as in bcg_k2a_rows.
-template <bool WID, typename T, typename Acc>
+// x += alpha p + omega s (p_in, s_in with a preconditioner: PRE),
+// r = s - omega t, and the sums (r^, r), ||W r||^2 and (weights present)
+// ||r||^2; WID as in bcg_k2a_rows.
+template <bool WID, bool PRE, typename T, typename Acc>
 __device__ __forceinline__ void bcg_k3_rows(const BcgArgs<T>& a, Acc alpha, Acc omega, Acc (&acc)[3]) {
   constexpr int R = Vec16<T>::R;
   BCG_VEC_LOOP(a, R) {
     if (i0 + R <= a.n && a.vec_ok) {
-      const Vec16<T> sv = vload(a.s + i0), pv = vload(a.p + i0), xv = vload(a.x + i0), tv = vload(a.t + i0),
+      const Vec16<T> sv = vload(a.s + i0), pv = vload(a.p_in + i0), xv = vload(a.x + i0), tv = vload(a.t + i0),
                      hv = vload(a.rh + i0);
+      Vec16<T> shv;
+      if (PRE) shv = vload(a.s_in + i0);
       Vec16<T> xo, ro;
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         const Acc sq = (Acc)sv.v[q];
-        xo.v[q] = (T)fma(omega, sq, fma(alpha, (Acc)pv.v[q], (Acc)xv.v[q]));
+        xo.v[q] = (T)fma(omega, PRE ? (Acc)shv.v[q] : sq, fma(alpha, (Acc)pv.v[q], (Acc)xv.v[q]));
         ro.v[q] = (T)fma(-omega, (Acc)tv.v[q], sq);
         const Acc rd = (Acc)ro.v[q];
         acc[0] = fma((Acc)hv.v[q], rd, acc[0]);
@@ -285,12 +292,12 @@ __device__ __forceinline__ void bcg_k3_rows(const BcgArgs<T>& a, Acc alpha, Acc 
       vstore(a.x + i0, xo);
       vstore(a.r + i0, ro);
     } else {
-      for (int i = i0; i < min(i0 + R, a.n); ++i) bcg_k3_row<WID>(a, i, alpha, omega, acc);
+      for (int i = i0; i < min(i0 + R, a.n); ++i) bcg_k3_row<WID, PRE>(a, i, alpha, omega, acc);
     }
   }
 }
 
-template <typename T>
+template <typename T, bool PRE = false>
 __global__ void __launch_bounds__(kBlock) bcg_k3(BcgArgs<T> a) {
   BcgState* S = a.S;
   if (a.unrolled && (S->stop || S->check)) return;
@@ -302,7 +309,7 @@ __global__ void __launch_bounds__(kBlock) bcg_k3(BcgArgs<T> a) {
   const Acc alpha = (Acc)S->alpha;
   if (S->halfexit) {
     for (int i = blockIdx.x * kBlock + threadIdx.x; i < a.n; i += gridDim.x * kBlock)
-      a.x[i] = (T)fma(alpha, (Acc)a.p[i], (Acc)a.x[i]);
+      a.x[i] = (T)fma(alpha, (Acc)a.p_in[i], (Acc)a.x[i]);
     if (grid_last(a.cnt) && threadIdx.x == 0) {
       S->iters += 1;
       S->mu_rec = S->mu_s;
@@ -315,8 +322,8 @@ __global__ void __launch_bounds__(kBlock) bcg_k3(BcgArgs<T> a) {
   const Acc omega = (Acc)S->omega;
   const bool wid = S->w_identity;
   Acc acc[3] = {Acc(0), Acc(0), Acc(0)};
-  if (wid) bcg_k3_rows<true>(a, alpha, omega, acc);
-  else bcg_k3_rows<false>(a, alpha, omega, acc);
+  if (wid) bcg_k3_rows<true, PRE>(a, alpha, omega, acc);
+  else bcg_k3_rows<false, PRE>(a, alpha, omega, acc);
   const double accd[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
   block_sum<3, kBlock>(accd, sm, blk);
   if (grid_sum(blk, 3, a.red, tot) && threadIdx.x == 0) {

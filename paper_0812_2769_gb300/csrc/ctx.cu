@@ -176,6 +176,7 @@ gsk_status gsk_profile_solve(gsk_ctx* ctx, int solver, const gsk_csr* A, const v
   if (opts_in) opts = *opts_in;
   else gsk_opts_default(&opts);
   if (opts.precision != GSK_PREC_F64) return ctx->fail(GSK_ERR_ARG, "profiling runs the FP64 solvers");
+  if (opts.precond) return ctx->fail(GSK_ERR_ARG, "profiling runs the solvers without a preconditioner");
   gsk::LaunchTimer T;
   T.ctx = ctx;
   T.st = (cudaStream_t)stream;

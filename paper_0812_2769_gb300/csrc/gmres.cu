@@ -2,12 +2,19 @@
 // point and the stream-mode profiler.  The kernels are in gmres_kernels.cuh.
 #include "gmres_kernels.cuh"
 #include "graph.hpp"
+#include "ilu.cuh"
 
 namespace gsk {
 
 // ------------------------------------------------------------------ host
 
+// launches of the right-preconditioned cycle (ILU(0)): z = M^-1 v_j before
+// the product of step j; z = M^-1 u and x += z after the cycle's update u
+constexpr int kGmIluV = 1000, kGmIluU = 1001, kGmXadd = 1002;
+
 struct GmPlan {
+  const gsk_ilu0* pre = nullptr;
+  double *zbuf = nullptr, *ubuf = nullptr;
   int g_tile, g_gx, wmode, KP, nclass;
   int g_gd[kGmClasses], g_gb[kGmClasses], g_gc[kGmClasses];
   GmArgs<double> a;
@@ -26,6 +33,22 @@ static void gm_launch_kp(gsk_ctx* ctx, GmPlan& P, int k, cudaStream_t s) {
     case kKGmGy: gm_gy<double><<<1, 32, 0, s>>>(a); break;
     case kKGmGx: gm_gx<double, KP><<<P.g_gx, kBlock, 0, s>>>(a); break;
     case kKGmGr: gm_residual<double, false><<<P.g_tile, kBlock, 0, s>>>(a); break;
+    case kGmIluV: {
+      IluGate g = {};
+      g.base = a.V;
+      g.col = &a.S->j;
+      g.stride = a.ldv;
+      g.run_if = a.unrolled ? &a.S->cont : nullptr;
+      ilu_launch_apply(ctx, P.pre, g, P.zbuf, s);
+      break;
+    }
+    case kGmIluU: {
+      IluGate g = {};
+      g.base = P.ubuf;
+      ilu_launch_apply(ctx, P.pre, g, P.zbuf, s);
+      break;
+    }
+    case kGmXadd: gm_xadd<double><<<P.g_gx, kBlock, 0, s>>>(a); break;
   }
 }
 
@@ -115,10 +138,14 @@ static gsk_status gm_record(gsk_ctx* ctx, GmPlan& P, cudaGraphExec_t* exec_out) 
   GSK_CK(c1.begin(cs, obody));
   for (int j = 0; j < a.m; ++j) {
     const int c = gm_kclass(j + 1);
+    if (P.pre) gm_launch(ctx, P, kGmIluV, cs);
     gm_launch(ctx, P, kKGmGa, cs);
     for (int k : {kKGmGd, kKGmGb, kKGmGc}) gm_launch_cgs(P, k, c, cs);
   }
-  for (int k : {kKGmGy, kKGmGx, kKGmGr}) gm_launch(ctx, P, k, cs);
+  for (int k : {kKGmGy, kKGmGx}) gm_launch(ctx, P, k, cs);
+  if (P.pre)
+    for (int k : {kGmIluU, kGmXadd}) gm_launch(ctx, P, k, cs);
+  gm_launch(ctx, P, kKGmGr, cs);
   GSK_CK(c1.end());
   GSK_CK(cudaGraphInstantiate(exec_out, top, 0));
   return GSK_OK;
@@ -130,6 +157,9 @@ static gsk_status gm_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, void
   if (!(tol >= 0.0) || opts.maxit < 0) return ctx->fail(GSK_ERR_ARG, "bad tol/maxit");
   if (A->n > 0 && (!b || !x)) return ctx->fail(GSK_ERR_ARG, "NULL b or x");
   const int n = A->n;
+  P.pre = opts.precond;
+  if (P.pre && (P.pre->n != n || P.pre->device != ctx->device))
+    return ctx->fail(GSK_ERR_ARG, "the preconditioner belongs to another matrix or device");
   P.wmode = opts.weights ? 2 : (opts.metric == GSK_METRIC_PLAIN ? 1 : 0);
   P.KP = m <= 16 ? 16 : (m <= 32 ? 32 : 64);
   // tile (SpMV) kernels carry no per-column accumulators: full occupancy
@@ -158,6 +188,8 @@ static gsk_status gm_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, void
     a.sig = ar.take<double>(m + 1);
     a.V = ar.take<double>((size_t)ldv * (m + 1));
     P.wbuf = P.wmode == 0 ? ar.take<double>(n) : nullptr;
+    P.zbuf = P.pre ? ar.take<double>(n) : nullptr;
+    P.ubuf = P.pre ? ar.take<double>(n) : nullptr;
   };
   Arena sizing;
   layout(sizing);
@@ -177,6 +209,8 @@ static gsk_status gm_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, void
   a.w = P.wmode == 0 ? P.wbuf : (P.wmode == 2 ? opts.weights : nullptr);
   a.in_graph = 0;
   a.vec_ok = ((uintptr_t)x % 16) == 0;
+  a.zin = P.pre ? P.zbuf : nullptr;
+  a.u_out = P.pre ? P.ubuf : nullptr;
   GmState& hs = P.host_state;
   std::memset(&hs, 0, sizeof(hs));
   hs.tol = tol;
@@ -262,7 +296,7 @@ extern "C" gsk_status gmres_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b,
   }
   std::vector<uint64_t> key = {0, (uint64_t)A->n, (uint64_t)A->nnz, (uint64_t)m, (uint64_t)A->rowptr,
                                (uint64_t)A->colidx, (uint64_t)A->val, (uint64_t)b, (uint64_t)x, (uint64_t)P.wmode,
-                               (uint64_t)P.a.w, (uint64_t)ctx->ws};
+                               (uint64_t)P.a.w, (uint64_t)ctx->ws, (uint64_t)(P.pre ? P.pre->serial : 0)};
   GraphEntry* ge = ctx->find_graph(key);
   if (!ge) {
     cudaGraphExec_t ex = nullptr;
@@ -280,5 +314,6 @@ extern "C" gsk_status gmres_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b,
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
   *info = gsk_info{out.iters, out.restarts, 0, 0, out.conv, out.mu_true, out.est, ms};
+  if (P.pre && (s = ilu_read_err(ctx, P.pre, st)) != GSK_OK) return s;
   return err_bits_status(ctx, bits);
 }

@@ -62,6 +62,11 @@ struct GmArgs {
   cudaGraphConditionalHandle h_outer, h_inner;
   int in_graph;
   int vec_ok;  // x is 16-byte aligned: 128-bit loads in the x update
+  // right preconditioning (x = M^-1 u): the product of a step takes
+  // zin = M^-1 v_j instead of v_j, and the cycle's update V (sig .* y) goes
+  // to u_out (then x += M^-1 u_out); both null without a preconditioner
+  const T* zin;
+  T* u_out;
   // unrolled cycle: the graph holds the m steps of a cycle as a chain (step j
   // with the basis kernels of class gm_kclass(j + 1)) instead of an inner
   // WHILE node; once the cycle has ended (S->cont == 0) the remaining steps'
@@ -194,7 +199,7 @@ __global__ void __launch_bounds__(kBlock) gm_ga(GmArgs<T> a) {
   const GmState* S = a.S;
   if (a.unrolled && !S->cont) return;  // the cycle ended at an earlier step
   const int j = S->j;
-  const T* vj = a.V + (long long)j * a.ldv;
+  const T* vj = a.zin ? a.zin : a.V + (long long)j * a.ldv;
   T* __restrict__ wout = a.V + (long long)(j + 1) * a.ldv;
   using Acc = typename AccOf<T>::type;
   const Acc sj = (Acc)a.sig[j];
@@ -469,12 +474,21 @@ __global__ void __launch_bounds__(kBlock) gm_gx(GmArgs<T> a) {
   for (int c = threadIdx.x; c < k; c += kBlock) coef[c] = a.sig[c] * a.y[c];
   __syncthreads();
   constexpr int R = Vec16<T>::R;
+  // without a preconditioner x += V (sig .* y); with one u = V (sig .* y)
+  T* dst = a.u_out ? a.u_out : a.x;
+  const bool add = a.u_out == nullptr;
+  const bool vec = add ? a.vec_ok != 0 : true;  // u_out is workspace (aligned)
   GM_VEC_LOOP(a, R) {
-    if (i0 + R <= a.n && a.vec_ok) {
-      const Vec16<T> x0 = vload(a.x + i0);
+    if (i0 + R <= a.n && vec) {
       double x[R];
+      if (add) {
+        const Vec16<T> x0 = vload(a.x + i0);
 #pragma unroll
-      for (int r = 0; r < R; ++r) x[r] = (double)x0.v[r];
+        for (int r = 0; r < R; ++r) x[r] = (double)x0.v[r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = 0.0;
+      }
       for_columns<KP>(k, [&](int c) {
         const Vec16<T> v = vload(a.V + (long long)c * a.ldv + i0);
 #pragma unroll
@@ -483,15 +497,21 @@ __global__ void __launch_bounds__(kBlock) gm_gx(GmArgs<T> a) {
       Vec16<T> xo;
 #pragma unroll
       for (int r = 0; r < R; ++r) xo.v[r] = (T)x[r];
-      vstore(a.x + i0, xo);
+      vstore(dst + i0, xo);
     } else {
       for (int i = i0; i < min(i0 + R, a.n); ++i) {
-        double x = (double)a.x[i];
+        double x = add ? (double)a.x[i] : 0.0;
         for_columns<KP>(k, [&](int c) { x = fma((double)a.V[(long long)c * a.ldv + i], coef[c], x); });
-        a.x[i] = (T)x;
+        dst[i] = (T)x;
       }
     }
   }
+}
+
+// x += z (the preconditioned cycle's correction z = M^-1 V (sig .* y), in zin).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) gm_xadd(GmArgs<T> a) {
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < a.n; i += gridDim.x * kBlock) a.x[i] += a.zin[i];
 }
 
 }  // namespace gsk

@@ -370,6 +370,8 @@ static gsk_status mx_prepare(gsk_ctx* ctx, int solver, const gsk_csr* A, const v
     bi.v = v32;
     bi.s = s32;
     bi.t = t32;
+    bi.p_in = bi.p;
+    bi.s_in = bi.s;
     bi.w = nullptr;
     bi.S = a.Sb;
     bi.red = a.red;
@@ -594,10 +596,12 @@ static gsk_status mx_solve(gsk_ctx* ctx, int solver, const gsk_csr* A, const voi
 
 gsk_status gmres_solve_mixed(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, int m, double tol,
                              const gsk_opts* opts, gsk_info* info, void* stream) {
+  if (opts && opts->precond) return ctx->fail(GSK_ERR_ARG, "no preconditioner with mixed precision");
   return gsk::mx_solve(ctx, 0, A, b, x, m, tol, opts, info, stream);
 }
 
 gsk_status bicgstab_solve_mixed(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, double tol,
                                 const gsk_opts* opts, gsk_info* info, void* stream) {
+  if (opts && opts->precond) return ctx->fail(GSK_ERR_ARG, "no preconditioner with mixed precision");
   return gsk::mx_solve(ctx, 1, A, b, x, 30, tol, opts, info, stream);
 }
