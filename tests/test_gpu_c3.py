@@ -1,0 +1,100 @@
+"""The 256^3 configuration (16.8 M unknowns, 117 M nonzeros; coefficients
+log-uniform in [1e-3, 1e3] on an 8^3 partition, convection U[-30, 30]^3 per
+cell) on the GPU path at full size, checked where the oracle cannot run a
+whole solve: GS(2) and the product on sampled rows (rows are independent, so
+the oracle runs on the sub-matrix), and properties of the solves that hold
+at any size: the reported metric equals the oracle's recomputation from the
+returned x, and FP32 inner solves with FP64 refinement reach the residual of
+plain FP64 GMRES(30) in the same number of steps.
+
+On this system restarted GMRES(30) stagnates near a relative residual of
+1e-7 (20,000 steps, FP64 and mixed alike) and Bi-CGSTAB breaks down: the
+cell Peclet number reaches ~60 where a = 1e-3, beyond what central
+differences keep well conditioned; 1e-10 is not reached by either method."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import gsk, to_dev
+from problems import configs
+
+pytestmark = pytest.mark.gpu
+
+_SYS = {}
+
+
+def _c3():
+    if "s" not in _SYS:
+        _SYS["s"] = configs.c3(256)
+        _SYS["w"] = oracle.metric_weights(_SYS["s"].rowptr, _SYS["s"].val)
+    return _SYS["s"], _SYS["w"]
+
+
+def _sub(s, idx, val=None):
+    val = s.val if val is None else val
+    lens = s.rowptr[idx + 1] - s.rowptr[idx]
+    rp = np.zeros(len(idx) + 1, dtype=np.int32)
+    rp[1:] = np.cumsum(lens)
+    gather = np.concatenate([np.arange(s.rowptr[i], s.rowptr[i + 1]) for i in idx])
+    return rp, s.colidx[gather], val[gather], gather
+
+
+def test_c3_gs_and_spmv_on_sampled_rows():
+    import torch
+
+    g = gsk()
+    s, _ = _c3()
+    A, b = to_dev(g, s)
+    idx = np.unique(np.concatenate([np.random.default_rng(21).choice(s.n, 3000, replace=False), [0, s.n - 1]]))
+    x = np.random.default_rng(22).normal(size=s.n)
+    y = torch.empty(s.n, dtype=torch.float64, device="cuda")
+    g.gsk_spmv(A, torch.as_tensor(x, device="cuda"), y)
+    rp, ci, va, _ = _sub(s, idx)
+    assert np.allclose(y.cpu().numpy()[idx], oracle.spmv(rp, ci, va, x), rtol=1e-13, atol=1e-12)
+    g.gs_scale(A, b, p=2.0)
+    val_or, b_or, _ = oracle.gs_scale(rp, ci, va, s.b[idx], 2.0)
+    _, _, _, gather = _sub(s, idx)
+    got = A.val.cpu().numpy()[gather]
+    assert np.all(np.abs(got - val_or) <= 1e-14 * np.abs(val_or))
+    assert np.allclose(b.cpu().numpy()[idx], b_or, rtol=1e-14, atol=0)
+
+
+def _gmres(g, s, precision, steps):
+    import torch
+
+    A, b = to_dev(g, s)
+    g.gs_scale(A, b, p=2.0)
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    info = g.gmres_solve(A, b, x, m=30, tol=1e-10, options=g.opts(precision=precision, maxit=steps))
+    return x.cpu().numpy(), info
+
+
+def test_c3_mixed_refinement_matches_fp64_gmres():
+    g = gsk()
+    s, w = _c3()
+    x64, i64 = _gmres(g, s, g.PREC_F64, 1500)
+    x32, i32 = _gmres(g, s, g.PREC_MIXED, 1500)
+    for x, info in ((x64, i64), (x32, i32)):
+        assert np.all(np.isfinite(x))
+        rr = oracle.relres(s.rowptr, s.colidx, s.val, s.b, x, w=w)  # GS(2)-scaled metric of A x = b
+        assert abs(rr - info["relres_true"]) <= 1e-6 * rr, (rr, info)
+        assert rr < 1e-3
+    # the FP32 inner iterations with FP64 refinement keep pace with FP64
+    assert i32["relres_true"] <= 2.0 * i64["relres_true"], (i32, i64)
+    assert i32["refinements"] >= 1
+
+
+def test_c3_bicgstab_reports_its_metric():
+    import torch
+
+    g = gsk()
+    s, w = _c3()
+    A, b = to_dev(g, s)
+    g.gs_scale(A, b, p=2.0)
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    info = g.bicgstab_solve(A, b, x, tol=1e-10, options=g.opts(maxit=2000))
+    xh = x.cpu().numpy()
+    assert np.all(np.isfinite(xh))
+    rr = oracle.relres(s.rowptr, s.colidx, s.val, s.b, xh, w=w)
+    assert abs(rr - info["relres_true"]) <= 1e-6 * rr, (rr, info)
+    assert info["conv"] in (g.CONVERGED, g.MAXIT, g.BREAKDOWN, g.STAGNATED)
