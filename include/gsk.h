@@ -104,6 +104,14 @@ typedef struct {
                              residual and the stopping metric stay those of
                              A x = b; NULL (the default) = none.  FP64 solvers
                              only (GSK_ERR_ARG with GSK_PREC_MIXED) */
+  int32_t batch_block;    /* batched solvers: threads per block, one block per
+                             system: 128, 256 or 512; 0 (the default) = 256.
+                             The autotuner (paper_0812_2769_gb300.autotune)
+                             picks it by timing candidates */
+  int32_t batch_large_n;  /* batched solvers: systems with more rows than
+                             this are solved one at a time by the grid-wide
+                             solvers instead of by one block; 0 (the default)
+                             = every system takes one block */
 } gsk_opts;
 
 /* Result of a solve (host memory). */
@@ -281,12 +289,33 @@ gsk_status bicgstab_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x
  *           finished by FP64 Bi-CGSTAB from its current x
  *   infos   host array [nsys] or NULL; status host array [nsys] or NULL
  *           (per-system gsk_status: GSK_ERR_ZERO_ROW / NONFINITE / ARG).
+ *           batch_block (threads per block: 128, 256, 512; 0 = 256) and
+ *           batch_large_n (systems with more rows are solved first, one at
+ *           a time, by gs_scale and the grid-wide solver with the same
+ *           options; 0 = none) shape the launch
+ *   infos   host array [nsys] or NULL; status host array [nsys] or NULL
+ *           (per-system gsk_status: GSK_ERR_ZERO_ROW / NONFINITE / ARG).
  * When infos or status is given the call synchronises `stream`; it returns
  * the first failing system's status (the others are still solved).
  */
 gsk_status bicgstab_solve_batched(gsk_ctx* ctx, int nsys, const gsk_csr* A, void* const* b, void* const* x,
                                   const double* p, double tol, const gsk_opts* opts, gsk_info* infos,
                                   int32_t* status, void* stream);
+
+/*
+ * gmres_solve_batched -- GS(p) then restarted GMRES(m_i) with classical
+ * Gram-Schmidt applied twice (Sec. 2) on nsys independent systems in one
+ * persistent launch, one thread block per system (the basis in the block's
+ * scratch), with the cycle and stopping rules of gmres_solve.  Arguments as
+ * bicgstab_solve_batched, plus
+ *   m       host array [nsys]: restart length of each system, 1..64
+ * The one-block path is FP64; precision GSK_PREC_MIXED is accepted only for
+ * systems routed to the grid-wide solver by batch_large_n (GSK_ERR_ARG
+ * otherwise).  Bit-identical alone and in any batch for a given batch_block.
+ */
+gsk_status gmres_solve_batched(gsk_ctx* ctx, int nsys, const gsk_csr* A, void* const* b, void* const* x,
+                               const double* p, const int* m, double tol, const gsk_opts* opts, gsk_info* infos,
+                               int32_t* status, void* stream);
 
 /* One timed kernel launch of gsk_profile_solve. */
 typedef struct {

@@ -49,7 +49,8 @@ class CsrC(C.Structure):
 class OptsC(C.Structure):
     _fields_ = [("maxit", C.c_int32), ("refresh", C.c_int32), ("precision", C.c_int32), ("metric", C.c_int32),
                 ("weights", C.c_void_p), ("inner_tol", C.c_double), ("inner_maxit", C.c_int32),
-                ("max_refinements", C.c_int32), ("precond", C.c_void_p)]
+                ("max_refinements", C.c_int32), ("precond", C.c_void_p), ("batch_block", C.c_int32),
+                ("batch_large_n", C.c_int32)]
 
 
 class InfoC(C.Structure):
@@ -94,6 +95,9 @@ SIGNATURES = {
     "bicgstab_solve_batched": ([C.c_void_p, C.c_int, C.POINTER(CsrC), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                 C.POINTER(C.c_double), C.c_double, C.POINTER(OptsC), C.POINTER(InfoC),
                                 C.POINTER(C.c_int32), C.c_void_p], C.c_int),
+    "gmres_solve_batched": ([C.c_void_p, C.c_int, C.POINTER(CsrC), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                             C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_double, C.POINTER(OptsC),
+                             C.POINTER(InfoC), C.POINTER(C.c_int32), C.c_void_p], C.c_int),
     "gsk_profile_solve": ([C.c_void_p, C.c_int, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                            C.POINTER(OptsC), C.c_int, C.POINTER(LaunchRecordC), C.c_int, C.POINTER(C.c_int),
                            C.POINTER(InfoC), C.c_void_p], C.c_int),
@@ -216,15 +220,17 @@ def _ptr(t):
 
 
 def opts(maxit=10000, refresh=3, precision=PREC_F64, metric=METRIC_GS2, weights=None, inner_tol=1e-5,
-         inner_maxit=0, max_refinements=0, precond=None) -> OptsC:
+         inner_maxit=0, max_refinements=0, precond=None, batch_block=0, batch_large_n=0) -> OptsC:
     """Solver options; precond: an Ilu0 of the matrix being solved (applied on
-    the right), or None."""
+    the right), or None; batch_block / batch_large_n: the batched solvers'
+    block size and grid-wide threshold (0 = defaults; see autotune)."""
     o = OptsC()
     lib().gsk_opts_default(C.byref(o))
     o.maxit, o.refresh, o.precision, o.metric = maxit, refresh, precision, metric
     o.weights = None if weights is None else weights.data_ptr()
     o.inner_tol, o.inner_maxit, o.max_refinements = inner_tol, inner_maxit, max_refinements
     o.precond = None if precond is None else precond.handle
+    o.batch_block, o.batch_large_n = batch_block, batch_large_n
     return o
 
 
@@ -363,6 +369,32 @@ def bicgstab_solve_batched(As, bs, xs, p=2.0, tol: float = 1e-8, options: OptsC 
     o = options if options is not None else opts()
     st = lib().bicgstab_solve_batched(ctx.handle, n, arr, bp, xp, pa, float(tol), C.byref(o), infos, stat,
                                       _stream_ptr(stream))
+    if check and st != OK:
+        ctx.check(st)
+    if not sync:
+        return None
+    return [i.as_dict() for i in infos], list(stat)
+
+
+def gmres_solve_batched(As, bs, xs, m=30, p=2.0, tol: float = 1e-8, options: OptsC | None = None,
+                        ctx: Context | None = None, stream=None, sync: bool = True, check: bool = True):
+    """GS(p) + GMRES(m) on many systems in one persistent launch (one block per
+    system; FP64).  m, p: one value or a list.  Returns (list of info dicts,
+    list of statuses) when sync."""
+    n = len(As)
+    ctx = ctx or default_context(As[0].val.device.index or 0 if n else 0)
+    arr = (CsrC * n)(*[A.c() for A in As])
+    bp = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    pv = [p] * n if not isinstance(p, (list, tuple)) else list(p)
+    mv = [m] * n if not isinstance(m, (list, tuple)) else list(m)
+    pa = (C.c_double * n)(*[float(v) for v in pv])
+    ma = (C.c_int * n)(*[int(v) for v in mv])
+    infos = (InfoC * n)() if sync else None
+    stat = (C.c_int32 * n)() if sync else None
+    o = options if options is not None else opts()
+    st = lib().gmres_solve_batched(ctx.handle, n, arr, bp, xp, pa, ma, float(tol), C.byref(o), infos, stat,
+                                   _stream_ptr(stream))
     if check and st != OK:
         ctx.check(st)
     if not sync:

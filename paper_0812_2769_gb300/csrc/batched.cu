@@ -8,6 +8,11 @@
 // waiting on other blocks.  A system's arithmetic depends only on the system
 // and the block size, so its result is bit-identical alone and in any batch.
 //
+// GMRES(m) (FP64, batch_gmres) runs the same way, one block per system, with
+// the basis in the block's slot memory.
+// The block size (128, 256 or 512 threads) is a template parameter chosen
+// per call (gsk_opts.batch_block, picked by the autotuner).
+//
 // Two precisions (template MIXED):
 //   FP64   Bi-CGSTAB as bicgstab_solve: recursive residual, true-residual
 //          confirmation and up to `refresh` restarts, breakdown tests.
@@ -28,7 +33,6 @@
 
 namespace gsk {
 
-constexpr int kBatchBlock = 256;
 // mixed precision: FP32 iterations per refinement step when inner_maxit is 0
 // (short inner solves let the FP64 refinement and the escalation test act
 // early on systems whose conditioning is too much for FP32)
@@ -45,13 +49,14 @@ struct BatchSys {
 };
 
 struct BatchOut {
-  int iters, refreshes, refinements, conv, status;
+  int iters, restarts, refreshes, refinements, conv, status;
   double relres_true, relres_rec;
 };
 
 struct BatchParams {
   const BatchSys* sys;
   const int* order;
+  const int* mvec;  // GMRES: restart length per system
   int nsys;
   unsigned* queue;
   BatchOut* out;
@@ -61,18 +66,18 @@ struct BatchParams {
   int maxit, refresh, inner_maxit, metric_plain;
 };
 
-template <int NV>
+template <int NV, int BS>
 __device__ __forceinline__ void bsum(const double (&v)[NV], double* sm, double* res) {
-  block_sum<NV, kBatchBlock>(v, sm, res);
+  block_sum<NV, BS>(v, sm, res);
 }
 
 // y = A x for one system, thread per row; bad indices flag *err.
-template <typename T>
+template <int BS, typename T>
 __device__ __forceinline__ void block_spmv(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                            const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y,
                                            int* err) {
   using Acc = typename AccOf<T>::type;
-  for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+  for (int i = threadIdx.x; i < n; i += BS) {
     const int rs = rowptr[i], re = rowptr[i + 1];
     Acc sum = Acc(0);
     for (int k = rs; k < re; ++k) {
@@ -90,7 +95,7 @@ __device__ __forceinline__ void block_spmv(int n, const int* __restrict__ rowptr
 // restart_on_breakdown (used only when a mixed-precision system is finished
 // in FP64): a breakdown restarts from the true residual while refreshes are
 // left, instead of ending the solve.
-template <typename T>
+template <int BS, typename T>
 __device__ void block_bicgstab(int n, const int* rowptr, const int* colidx, const T* val, const T* rhs, T* x,
                                T* r, T* rh, T* p, T* v, T* s, T* t, const double* w, double tol, int maxit,
                                int refresh, bool confirm, double brk, double* sm, int* err, BatchOut& o,
@@ -99,12 +104,12 @@ __device__ void block_bicgstab(int n, const int* rowptr, const int* colidx, cons
   __shared__ double res[4];
   const bool wid = (w == nullptr);
   // r = rhs - A x
-  block_spmv(n, rowptr, colidx, val, x, t, err);
+  block_spmv<BS>(n, rowptr, colidx, val, x, t, err);
   __syncthreads();
   double acc2[2] = {0.0, 0.0};
   {
     Acc a0 = 0, a1 = 0;
-    for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+    for (int i = threadIdx.x; i < n; i += BS) {
       const T ri = (T)((Acc)rhs[i] - (Acc)t[i]);
       r[i] = ri;
       rh[i] = ri;
@@ -116,7 +121,7 @@ __device__ void block_bicgstab(int n, const int* rowptr, const int* colidx, cons
     acc2[0] = a0;
     acc2[1] = a1;
   }
-  bsum<2>(acc2, sm, res);
+  bsum<2, BS>(acc2, sm, res);
   const double mu0 = sqrt(res[0]);
   double rho = res[1], rhn = sqrt(res[1]);
   o.iters = 0;
@@ -151,55 +156,55 @@ __device__ void block_bicgstab(int n, const int* rowptr, const int* colidx, cons
         o.conv = GSK_MAXIT;
         goto done;
       }
-      block_spmv(n, rowptr, colidx, val, p, v, err);
+      block_spmv<BS>(n, rowptr, colidx, val, p, v, err);
       __syncthreads();
       {
         Acc a0 = 0, a1 = 0;
-        for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+        for (int i = threadIdx.x; i < n; i += BS) {
           a0 = fma((Acc)rh[i], (Acc)v[i], a0);
           a1 = fma((Acc)v[i], (Acc)v[i], a1);
         }
         double ad[2] = {(double)a0, (double)a1};
-        bsum<2>(ad, sm, res);
+        bsum<2, BS>(ad, sm, res);
       }
       const double sigma = res[0], vn = sqrt(res[1]);
       if (!(fabs(sigma) > brk * rhn * vn)) BCG_BREAKDOWN
       const double alpha = rho / sigma;
       {
         Acc a0 = 0;
-        for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+        for (int i = threadIdx.x; i < n; i += BS) {
           const T si = (T)fma(-(Acc)alpha, (Acc)v[i], (Acc)r[i]);
           s[i] = si;
           const Acc ws = (Acc)(wid ? 1.0 : w[i]) * (Acc)si;
           a0 = fma(ws, ws, a0);
         }
         double ad[1] = {(double)a0};
-        bsum<1>(ad, sm, res);
+        bsum<1, BS>(ad, sm, res);
       }
       const double mus = sqrt(res[0]) / mu0;
       if (mus < tol) {
-        for (int i = threadIdx.x; i < n; i += kBatchBlock) x[i] = (T)fma((Acc)alpha, (Acc)p[i], (Acc)x[i]);
+        for (int i = threadIdx.x; i < n; i += BS) x[i] = (T)fma((Acc)alpha, (Acc)p[i], (Acc)x[i]);
         o.iters += 1;
         o.relres_rec = mus;
         check_true = true;
         break;
       }
-      block_spmv(n, rowptr, colidx, val, s, t, err);
+      block_spmv<BS>(n, rowptr, colidx, val, s, t, err);
       __syncthreads();
       {
         Acc a0 = 0, a1 = 0;
-        for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+        for (int i = threadIdx.x; i < n; i += BS) {
           a0 = fma((Acc)t[i], (Acc)s[i], a0);
           a1 = fma((Acc)t[i], (Acc)t[i], a1);
         }
         double ad[2] = {(double)a0, (double)a1};
-        bsum<2>(ad, sm, res);
+        bsum<2, BS>(ad, sm, res);
       }
       if (!(res[1] > 0.0)) BCG_BREAKDOWN
       const double omega = res[0] / res[1];
       {
         Acc a0 = 0, a1 = 0, a2 = 0;
-        for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+        for (int i = threadIdx.x; i < n; i += BS) {
           const Acc si = (Acc)s[i];
           x[i] = (T)fma((Acc)omega, si, fma((Acc)alpha, (Acc)p[i], (Acc)x[i]));
           const T ri = (T)fma(-(Acc)omega, (Acc)t[i], si);
@@ -210,7 +215,7 @@ __device__ void block_bicgstab(int n, const int* rowptr, const int* colidx, cons
           a2 = fma(rd, rd, a2);
         }
         double ad[3] = {(double)a0, (double)a1, (double)a2};
-        bsum<3>(ad, sm, res);
+        bsum<3, BS>(ad, sm, res);
       }
       o.iters += 1;
       const double mur = sqrt(res[1]) / mu0;
@@ -224,7 +229,7 @@ __device__ void block_bicgstab(int n, const int* rowptr, const int* colidx, cons
       if (!(fabs(rho1) > brk * rhn * rn)) BCG_BREAKDOWN
       const double beta = (rho1 / rho) * (alpha / omega);
       rho = rho1;
-      for (int i = threadIdx.x; i < n; i += kBatchBlock)
+      for (int i = threadIdx.x; i < n; i += BS)
         p[i] = (T)fma((Acc)beta, fma(-(Acc)omega, (Acc)v[i], (Acc)p[i]), (Acc)r[i]);
       __syncthreads();
     }
@@ -234,11 +239,11 @@ __device__ void block_bicgstab(int n, const int* rowptr, const int* colidx, cons
     }
     // true residual
     __syncthreads();
-    block_spmv(n, rowptr, colidx, val, x, t, err);
+    block_spmv<BS>(n, rowptr, colidx, val, x, t, err);
     __syncthreads();
     {
       Acc a0 = 0, a1 = 0;
-      for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+      for (int i = threadIdx.x; i < n; i += BS) {
         const T ti = (T)((Acc)rhs[i] - (Acc)t[i]);
         t[i] = ti;
         const Acc wt = (Acc)(wid ? 1.0 : w[i]) * (Acc)ti;
@@ -246,7 +251,7 @@ __device__ void block_bicgstab(int n, const int* rowptr, const int* colidx, cons
         a1 = fma((Acc)ti, (Acc)ti, a1);
       }
       double ad[2] = {(double)a0, (double)a1};
-      bsum<2>(ad, sm, res);
+      bsum<2, BS>(ad, sm, res);
     }
     const double mu = sqrt(res[0]) / mu0;
     o.relres_true = mu;
@@ -260,7 +265,7 @@ __device__ void block_bicgstab(int n, const int* rowptr, const int* colidx, cons
     }
     refresh_left -= 1;
     o.refreshes += 1;
-    for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+    for (int i = threadIdx.x; i < n; i += BS) {
       r[i] = t[i];
       rh[i] = t[i];
       p[i] = t[i];
@@ -273,15 +278,15 @@ __device__ void block_bicgstab(int n, const int* rowptr, const int* colidx, cons
 done:
   if (confirm) {  // report the true metric of the returned x
     __syncthreads();
-    block_spmv(n, rowptr, colidx, val, x, t, err);
+    block_spmv<BS>(n, rowptr, colidx, val, x, t, err);
     __syncthreads();
     Acc a0 = 0;
-    for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+    for (int i = threadIdx.x; i < n; i += BS) {
       const Acc wt = (Acc)(wid ? 1.0 : w[i]) * ((Acc)rhs[i] - (Acc)t[i]);
       a0 = fma(wt, wt, a0);
     }
     double ad[1] = {(double)a0};
-    bsum<1>(ad, sm, res);
+    bsum<1, BS>(ad, sm, res);
     o.relres_true = sqrt(res[0]) / mu0;
   }
 }
@@ -290,13 +295,14 @@ done:
 // row is zero or non-finite); then the metric weights W2 = 1/||a_i||_2 of the
 // scaled rows into w2 (left unused when p = 2: the rows then have unit norm).
 // Returns false (and the status) on an input error.
+template <int BS>
 __device__ bool block_gs(const BatchSys& S, double* d, double* w2, bool need_w2, int* status) {
   __shared__ int s_err;
   if (threadIdx.x == 0) s_err = 0;
   __syncthreads();
   const bool scale = !(S.p != S.p);
   const int pm = scale ? pmode_of(S.p) : kP2;
-  for (int i = threadIdx.x; i < S.n; i += kBatchBlock) {
+  for (int i = threadIdx.x; i < S.n; i += BS) {
     const int rs = S.rowptr[i], re = S.rowptr[i + 1];
     if (rs < 0 || re < rs || re > S.nnz) {
       atomicOr(&s_err, kErrIndex);
@@ -311,7 +317,7 @@ __device__ bool block_gs(const BatchSys& S, double* d, double* w2, bool need_w2,
     *status = (s_err & kErrIndex) ? GSK_ERR_ARG : ((s_err & kErrNonFinite) ? GSK_ERR_NONFINITE : GSK_ERR_ZERO_ROW);
     return false;
   }
-  for (int i = threadIdx.x; i < S.n; i += kBatchBlock) {
+  for (int i = threadIdx.x; i < S.n; i += BS) {
     const int rs = S.rowptr[i], re = S.rowptr[i + 1];
     if (scale) {
       const double di = d[i];
@@ -328,9 +334,9 @@ __device__ bool block_gs(const BatchSys& S, double* d, double* w2, bool need_w2,
   return true;
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(kBatchBlock) batch_bicgstab(BatchParams P) {
-  __shared__ double sm[3 * kBatchBlock];
+template <int BS, bool MIXED>
+__global__ void __launch_bounds__(BS) batch_bicgstab(BatchParams P) {
+  __shared__ double sm[3 * BS];
   __shared__ int s_idx, s_err;
   char* slot = P.scratch + (long long)blockIdx.x * P.slot_bytes;
   for (;;) {
@@ -343,17 +349,17 @@ __global__ void __launch_bounds__(kBatchBlock) batch_bicgstab(BatchParams P) {
     if (s_idx >= P.nsys) break;
     const int id = P.order[s_idx];
     const BatchSys S = P.sys[id];
-    BatchOut o = {0, 0, 0, GSK_MAXIT, GSK_OK, 1.0, 1.0};
+    BatchOut o = {0, 0, 0, 0, GSK_MAXIT, GSK_OK, 1.0, 1.0};
     const int n = S.n;
     double* d = reinterpret_cast<double*>(slot);
     double* w2 = d + n;
     // after GS(2) the rows have unit norm: the metric weights are the identity
     const bool w_identity = P.metric_plain || S.p == 2.0;
-    const bool ok = block_gs(S, d, w2, !w_identity || MIXED, &o.status);
+    const bool ok = block_gs<BS>(S, d, w2, !w_identity || MIXED, &o.status);
     if (ok) {
       if (!MIXED) {
         double* v = w2 + n;
-        block_bicgstab<double>(n, S.rowptr, S.colidx, S.val, S.b, S.x, v, v + n, v + 2 * n, v + 3 * n, v + 4 * n,
+        block_bicgstab<BS, double>(n, S.rowptr, S.colidx, S.val, S.b, S.x, v, v + n, v + 2 * n, v + 3 * n, v + 4 * n,
                                v + 5 * n, w_identity ? nullptr : w2, P.tol, P.maxit, P.refresh, true, P.brk, sm,
                                &s_err, o);
       } else {
@@ -367,16 +373,16 @@ __global__ void __launch_bounds__(kBatchBlock) batch_bicgstab(BatchParams P) {
         float *x32 = f, *r = f + n, *rh = f + 2 * n, *p = f + 3 * n, *v = f + 4 * n, *s = f + 5 * n,
               *t = f + 6 * n, *rhs = f + 7 * n;
         __shared__ double res[2];
-        for (int i = threadIdx.x; i < n; i += kBatchBlock)
+        for (int i = threadIdx.x; i < n; i += BS)
           for (int k = S.rowptr[i]; k < S.rowptr[i + 1]; ++k) a32[k] = (float)(S.val[k] * w2[i]);
         double mu0 = -1.0, mu_prev = 1.0;
         int total = 0;
         for (int ref = 0;; ++ref) {
           __syncthreads();
-          block_spmv<double>(n, S.rowptr, S.colidx, S.val, S.x, r64, &s_err);
+          block_spmv<BS, double>(n, S.rowptr, S.colidx, S.val, S.x, r64, &s_err);
           __syncthreads();
           double a0 = 0.0, a1 = 0.0;
-          for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+          for (int i = threadIdx.x; i < n; i += BS) {
             const double ri = S.b[i] - r64[i];
             r64[i] = ri;
             const double wr = (w_identity ? 1.0 : w2[i]) * ri, w2r = w2[i] * ri;
@@ -384,7 +390,7 @@ __global__ void __launch_bounds__(kBatchBlock) batch_bicgstab(BatchParams P) {
             a1 = fma(w2r, w2r, a1);
           }
           double ad[2] = {a0, a1};
-          bsum<2>(ad, sm, res);
+          bsum<2, BS>(ad, sm, res);
           const double mw = sqrt(res[0]), rn = sqrt(res[1]);
           if (ref == 0) mu0 = mw;
           o.refinements = ref;
@@ -407,13 +413,13 @@ __global__ void __launch_bounds__(kBatchBlock) batch_bicgstab(BatchParams P) {
           if (!escalate) {
             mu_prev = mu;
             const double inv = 1.0 / rn;
-            for (int i = threadIdx.x; i < n; i += kBatchBlock) {
+            for (int i = threadIdx.x; i < n; i += BS) {
               rhs[i] = (float)(w2[i] * r64[i] * inv);
               x32[i] = 0.f;
             }
             __syncthreads();
-            BatchOut oi = {0, 0, 0, GSK_MAXIT, GSK_OK, 1.0, 1.0};
-            block_bicgstab<float>(n, S.rowptr, S.colidx, a32, rhs, x32, r, rh, p, v, s, t, nullptr, P.inner_tol,
+            BatchOut oi = {0, 0, 0, 0, GSK_MAXIT, GSK_OK, 1.0, 1.0};
+            block_bicgstab<BS, float>(n, S.rowptr, S.colidx, a32, rhs, x32, r, rh, p, v, s, t, nullptr, P.inner_tol,
                                   min(P.inner_maxit, P.maxit - total), 0, false, (double)FLT_EPSILON, sm, &s_err,
                                   oi);
             total += oi.iters;
@@ -422,17 +428,17 @@ __global__ void __launch_bounds__(kBatchBlock) batch_bicgstab(BatchParams P) {
             // a correction that is not finite, or an inner solve that made no
             // step, is not applied: the system goes to FP64 instead
             int bad = oi.iters == 0;
-            for (int i = threadIdx.x; i < n; i += kBatchBlock) bad |= !isfinite(x32[i]);
+            for (int i = threadIdx.x; i < n; i += BS) bad |= !isfinite(x32[i]);
             escalate = __syncthreads_or(bad) != 0;
             if (!escalate) {
-              for (int i = threadIdx.x; i < n; i += kBatchBlock) S.x[i] = fma(rn, (double)x32[i], S.x[i]);
+              for (int i = threadIdx.x; i < n; i += BS) S.x[i] = fma(rn, (double)x32[i], S.x[i]);
               continue;
             }
           }
           // escalate: FP64 Bi-CGSTAB on the remaining error, the tolerance
           // rescaled so that it is still relative to the first residual
-          BatchOut o64 = {0, 0, 0, GSK_MAXIT, GSK_OK, 1.0, 1.0};
-          block_bicgstab<double>(n, S.rowptr, S.colidx, S.val, S.b, S.x, v64, v64 + n, v64 + 2 * n, v64 + 3 * n,
+          BatchOut o64 = {0, 0, 0, 0, GSK_MAXIT, GSK_OK, 1.0, 1.0};
+          block_bicgstab<BS, double>(n, S.rowptr, S.colidx, S.val, S.b, S.x, v64, v64 + n, v64 + 2 * n, v64 + 3 * n,
                                  v64 + 4 * n, v64 + 5 * n, w_identity ? nullptr : w2, P.tol / mu, P.maxit - total,
                                  P.refresh > 10 ? P.refresh : 10, true, P.brk, sm, &s_err, o64, true);
           total += o64.iters;
@@ -452,6 +458,235 @@ __global__ void __launch_bounds__(kBatchBlock) batch_bicgstab(BatchParams P) {
   }
 }
 
+// ------------------------------------------------------------ batched GMRES
+
+// Per-block GMRES work arrays (slot memory, L2-resident while the block
+// works on its system).
+struct GmWork {
+  double *V, *H, *g, *cs, *sn, *y, *h;
+};
+
+// h[c] = (V_c, w) for c < k: the columns in chunks of 8 register
+// accumulators, one block reduction per chunk.
+template <int BS>
+__device__ void block_multidot(int n, int k, const double* V, const double* w, double* h, double* sm,
+                               double* res) {
+  for (int c0 = 0; c0 < k; c0 += 8) {
+    const int nc = min(8, k - c0);
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < n; i += BS) {
+      const double wi = w[i];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < nc) acc[q] = fma(V[(long long)(c0 + q) * n + i], wi, acc[q]);
+    }
+    bsum<8, BS>(acc, sm, res);
+    if (threadIdx.x < nc) h[c0 + threadIdx.x] = res[threadIdx.x];
+  }
+  __syncthreads();
+}
+
+// w -= sum_c h[c] V_c for c < k.
+template <int BS>
+__device__ void block_subtract(int n, int k, const double* V, double* w, const double* h) {
+  for (int i = threadIdx.x; i < n; i += BS) {
+    double wi = w[i];
+    for (int c = 0; c < k; ++c) wi = fma(-h[c], V[(long long)c * n + i], wi);
+    w[i] = wi;
+  }
+  __syncthreads();
+}
+
+// V[:, 0] = rhs - A x; res2 = (||W r||, ||r||).
+template <int BS>
+__device__ void block_gm_residual(int n, const int* rowptr, const int* colidx, const double* val,
+                                  const double* rhs, const double* x, const double* wgt, double* r, double* sm,
+                                  double* res, int* err, double& mu_w, double& nrm) {
+  block_spmv<BS, double>(n, rowptr, colidx, val, x, r, err);
+  __syncthreads();
+  double a0 = 0.0, a1 = 0.0;
+  for (int i = threadIdx.x; i < n; i += BS) {
+    const double ri = rhs[i] - r[i];
+    r[i] = ri;
+    const double wr = (wgt ? wgt[i] : 1.0) * ri;
+    a0 = fma(wr, wr, a0);
+    a1 = fma(ri, ri, a1);
+  }
+  double ad[2] = {a0, a1};
+  bsum<2, BS>(ad, sm, res);
+  mu_w = sqrt(res[0]);
+  nrm = sqrt(res[1]);
+}
+
+// Restarted GMRES(m) with classical Gram-Schmidt applied twice (Sec. 2) on
+// one system, block-local, with the cycle of gmres_solve: a normalised basis,
+// Givens rotations of the Hessenberg columns (one thread), the cycle ending
+// when |g_{j+1}| < tau ||r0||, at breakdown h_{j+1,j} <= 1e-14 ||A v_j||
+// (from the CGS coefficients and h_{j+1,j}), after m steps or at maxit; the
+// true metric ||W r|| / ||W r0|| decides convergence and tau is tightened by
+// tol / metric when the estimate met it but the metric did not.
+template <int BS>
+__device__ void block_gmres(int n, const int* rowptr, const int* colidx, const double* val, const double* rhs,
+                            double* x, const double* wgt, int m, double tol, int maxit, const GmWork& W,
+                            double* sm, int* err, BatchOut& o) {
+  __shared__ double res[8];
+  __shared__ double s_scal[3];
+  const int ld = m + 1;
+  double mu_w, beta;
+  block_gm_residual<BS>(n, rowptr, colidx, val, rhs, x, wgt, W.V, sm, res, err, mu_w, beta);
+  const double mu0 = mu_w, rho0 = beta;
+  o.iters = 0;
+  o.restarts = 0;
+  o.relres_rec = 1.0;
+  o.relres_true = 1.0;
+  o.conv = GSK_MAXIT;
+  if (!(mu0 > 0.0)) {
+    if (mu0 == 0.0) {
+      o.conv = GSK_CONVERGED;
+      o.relres_true = o.relres_rec = 0.0;
+    }
+    return;
+  }
+  double tau = tol;
+  for (;;) {
+    const double ib = 1.0 / beta;
+    for (int i = threadIdx.x; i < n; i += BS) W.V[i] *= ib;
+    if (threadIdx.x == 0) {
+      W.g[0] = beta;
+      for (int q = 1; q <= m; ++q) W.g[q] = 0.0;
+    }
+    __syncthreads();
+    int kcols = 0;
+    bool est_hit = false;
+    for (int j = 0; j < m && o.iters < maxit; ++j) {
+      double* w = W.V + (long long)(j + 1) * n;
+      block_spmv<BS, double>(n, rowptr, colidx, val, W.V + (long long)j * n, w, err);
+      __syncthreads();
+      const int k = j + 1;
+      double* hc = W.H + (long long)j * ld;
+      block_multidot<BS>(n, k, W.V, w, W.h, sm, res);
+      if (threadIdx.x < k) hc[threadIdx.x] = W.h[threadIdx.x];
+      block_subtract<BS>(n, k, W.V, w, W.h);
+      block_multidot<BS>(n, k, W.V, w, W.h, sm, res);
+      if (threadIdx.x < k) hc[threadIdx.x] += W.h[threadIdx.x];
+      block_subtract<BS>(n, k, W.V, w, W.h);
+      double a0 = 0.0;
+      for (int i = threadIdx.x; i < n; i += BS) a0 = fma(w[i], w[i], a0);
+      double ad[1] = {a0};
+      bsum<1, BS>(ad, sm, res);
+      const double hnext = sqrt(res[0]);
+      if (threadIdx.x == 0) {
+        double aw2 = hnext * hnext;  // ||A v_j||^2 = ||h||^2 + h_{j+1,j}^2
+        for (int c = 0; c <= j; ++c) aw2 = fma(hc[c], hc[c], aw2);
+        for (int q = 0; q < j; ++q) {
+          const double t0 = W.cs[q] * hc[q] + W.sn[q] * hc[q + 1];
+          const double t1 = -W.sn[q] * hc[q] + W.cs[q] * hc[q + 1];
+          hc[q] = t0;
+          hc[q + 1] = t1;
+        }
+        const double rho = hypot(hc[j], hnext);
+        const double c_ = rho == 0.0 ? 1.0 : hc[j] / rho, s_ = rho == 0.0 ? 0.0 : hnext / rho;
+        W.cs[j] = c_;
+        W.sn[j] = s_;
+        hc[j] = rho;
+        hc[j + 1] = 0.0;
+        const double gj = W.g[j];
+        W.g[j + 1] = -s_ * gj;
+        W.g[j] = c_ * gj;
+        const double est = fabs(W.g[j + 1]) / rho0;
+        s_scal[0] = est;
+        s_scal[1] = est < tau ? 1.0 : (hnext <= 1e-14 * sqrt(aw2) ? 2.0 : 0.0);
+        s_scal[2] = hnext;
+      }
+      __syncthreads();
+      o.iters += 1;
+      kcols = k;
+      o.relres_rec = s_scal[0];
+      if (s_scal[1] == 1.0) {
+        est_hit = true;
+        break;
+      }
+      if (s_scal[1] == 2.0) break;
+      const double ih = 1.0 / s_scal[2];
+      for (int i = threadIdx.x; i < n; i += BS) w[i] *= ih;
+      __syncthreads();
+    }
+    // H y = g by back substitution, then x += V y
+    if (threadIdx.x == 0) {
+      for (int i = kcols - 1; i >= 0; --i) {
+        double sacc = W.g[i];
+        for (int q = i + 1; q < kcols; ++q) sacc -= W.H[(long long)q * ld + i] * W.y[q];
+        W.y[i] = sacc / W.H[(long long)i * ld + i];
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += BS) {
+      double xi = x[i];
+      for (int c = 0; c < kcols; ++c) xi = fma(W.y[c], W.V[(long long)c * n + i], xi);
+      x[i] = xi;
+    }
+    __syncthreads();
+    block_gm_residual<BS>(n, rowptr, colidx, val, rhs, x, wgt, W.V, sm, res, err, mu_w, beta);
+    const double mu = mu_w / mu0;
+    o.relres_true = mu;
+    if (mu < tol) {
+      o.conv = GSK_CONVERGED;
+      return;
+    }
+    if (o.iters >= maxit || kcols == 0 || !(beta > 0.0)) {
+      o.conv = GSK_MAXIT;
+      return;
+    }
+    if (est_hit) tau = tau * (tol / mu);
+    o.restarts += 1;
+  }
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS) batch_gmres(BatchParams P) {
+  __shared__ double sm[8 * BS];
+  __shared__ int s_idx, s_err;
+  char* slot = P.scratch + (long long)blockIdx.x * P.slot_bytes;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_idx = (int)atomicAdd(P.queue, 1u);
+      s_err = 0;
+    }
+    __syncthreads();
+    if (s_idx >= P.nsys) break;
+    const int id = P.order[s_idx];
+    const BatchSys S = P.sys[id];
+    BatchOut o = {0, 0, 0, 0, GSK_MAXIT, GSK_OK, 1.0, 1.0};
+    const int n = S.n, m = P.mvec[id];
+    double* d = reinterpret_cast<double*>(slot);
+    double* w2 = d + n;
+    const bool w_identity = P.metric_plain || S.p == 2.0;
+    const bool ok = block_gs<BS>(S, d, w2, !w_identity, &o.status);
+    if (ok) {
+      GmWork W;
+      W.V = w2 + n;
+      W.H = W.V + (long long)(m + 1) * n;
+      W.g = W.H + (long long)(m + 1) * m;
+      W.cs = W.g + m + 1;
+      W.sn = W.cs + m;
+      W.y = W.sn + m;
+      W.h = W.y + m;
+      block_gmres<BS>(n, S.rowptr, S.colidx, S.val, S.b, S.x, w_identity ? nullptr : w2, m, P.tol, P.maxit, W, sm,
+                      &s_err, o);
+    }
+    __syncthreads();
+    if (s_err) o.status = GSK_ERR_ARG;
+    if (threadIdx.x == 0) P.out[id] = o;
+  }
+}
+
+static size_t batch_gmres_slot_bytes(int nmax, int mmax) {
+  // d, w2, V (m+1 columns), H, g, cs, sn, y, h
+  size_t b = 8 * ((size_t)nmax * (mmax + 3) + (size_t)(mmax + 1) * mmax + 5 * (size_t)(mmax + 1));
+  return (b + 255) / 256 * 256;
+}
+
 static size_t batch_slot_bytes(bool mixed, int nmax, int nnzmax) {
   // FP64: d, w2, six vectors.  Mixed: d, w2, six FP64 vectors (escalation),
   // the FP64 residual, (W2 A)_32 and eight FP32 vectors.
@@ -460,13 +695,32 @@ static size_t batch_slot_bytes(bool mixed, int nmax, int nnzmax) {
   return (b + 255) / 256 * 256;
 }
 
-}  // namespace gsk
+// One persistent launch of the solver over the systems in `order`.
+template <int BS>
+static void batch_launch(int solver, bool mixed, int grid, const BatchParams& P, cudaStream_t st) {
+  if (solver == 0) batch_gmres<BS><<<grid, BS, 0, st>>>(P);
+  else if (mixed) batch_bicgstab<BS, true><<<grid, BS, 0, st>>>(P);
+  else batch_bicgstab<BS, false><<<grid, BS, 0, st>>>(P);
+}
 
-using namespace gsk;
+template <int BS>
+static int batch_blocks_per_sm(int solver, bool mixed) {
+  int per_sm = 0;
+  cudaError_t e;
+  if (solver == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_gmres<BS>, BS, 0);
+  else if (mixed) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_bicgstab<BS, true>, BS, 0);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_bicgstab<BS, false>, BS, 0);
+  if (e != cudaSuccess) cudaGetLastError();
+  return (e != cudaSuccess || per_sm < 1) ? 1 : per_sm;
+}
 
-extern "C" gsk_status bicgstab_solve_batched(gsk_ctx* ctx, int nsys, const gsk_csr* A, void* const* b,
-                                             void* const* x, const double* p, double tol, const gsk_opts* opts_in,
-                                             gsk_info* infos, int32_t* status, void* stream) {
+// solver 0: GMRES(m[i]) (FP64), 1: Bi-CGSTAB (FP64 or mixed).  Systems with
+// more than opts.batch_large_n rows are solved first, one at a time, by the
+// grid-wide solvers (gs_scale, then gmres_solve / bicgstab_solve with the
+// same options); the others by one persistent launch, one block each.
+static gsk_status batch_solve(gsk_ctx* ctx, int solver, int nsys, const gsk_csr* A, void* const* b, void* const* x,
+                              const double* p, const int* mvec, double tol, const gsk_opts* opts_in, gsk_info* infos,
+                              int32_t* status, void* stream) {
   if (!ctx) return GSK_ERR_ARG;
   if (nsys < 0 || (nsys > 0 && (!A || !b || !x))) return ctx->fail(GSK_ERR_ARG, "bad batch arrays");
   gsk_opts opts;
@@ -476,10 +730,15 @@ extern "C" gsk_status bicgstab_solve_batched(gsk_ctx* ctx, int nsys, const gsk_c
     return ctx->fail(GSK_ERR_ARG, "bad tol/maxit/refresh/inner_tol");
   if (opts.weights) return ctx->fail(GSK_ERR_ARG, "the batched solver derives its metric weights itself");
   if (opts.precond) return ctx->fail(GSK_ERR_ARG, "the batched solver takes no preconditioner");
-  if (nsys == 0) return GSK_OK;
+  const int BS = opts.batch_block == 0 ? 256 : opts.batch_block;
+  if (BS != 128 && BS != 256 && BS != 512) return ctx->fail(GSK_ERR_ARG, "batch_block must be 0, 128, 256 or 512");
+  if (opts.batch_large_n < 0) return ctx->fail(GSK_ERR_ARG, "batch_large_n must be >= 0");
   const bool mixed = opts.precision == GSK_PREC_MIXED;
+  if (solver == 0 && !mixed && !mvec) return ctx->fail(GSK_ERR_ARG, "NULL m array");
+  if (nsys == 0) return GSK_OK;
   std::vector<BatchSys> hs(nsys);
-  int nmax = 0, nnzmax = 0;
+  std::vector<int> small, large;
+  int nmax = 0, nnzmax = 0, mmax = 1;
   for (int i = 0; i < nsys; ++i) {
     gsk_status s = check_csr(ctx, &A[i]);
     if (s != GSK_OK) return s;
@@ -487,62 +746,98 @@ extern "C" gsk_status bicgstab_solve_batched(gsk_ctx* ctx, int nsys, const gsk_c
     if (A[i].n > 0 && (!b[i] || !x[i])) return ctx->fail(GSK_ERR_ARG, "NULL b or x in the batch");
     const double pi = p ? p[i] : NAN;
     if (!(pi != pi) && !(pi >= 1.0)) return ctx->fail(GSK_ERR_ARG, "p must be >= 1, INFINITY or NaN");
+    if (solver == 0 && (!mvec || mvec[i] < 1 || mvec[i] > kMaxM)) return ctx->fail(GSK_ERR_ARG, "m must be in 1..64");
     hs[i] = BatchSys{A[i].n, A[i].nnz, A[i].rowptr, A[i].colidx, (double*)A[i].val, (double*)b[i], (double*)x[i], pi};
-    nmax = std::max(nmax, A[i].n);
-    nnzmax = std::max(nnzmax, A[i].nnz);
+    if (opts.batch_large_n > 0 && A[i].n > opts.batch_large_n) {
+      large.push_back(i);
+    } else {
+      small.push_back(i);
+      nmax = std::max(nmax, A[i].n);
+      nnzmax = std::max(nnzmax, A[i].nnz);
+      if (solver == 0) mmax = std::max(mmax, mvec[i]);
+    }
   }
-  // largest systems first
-  std::vector<int> order(nsys);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return hs[a].nnz > hs[c].nnz; });
-
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, mixed ? batch_bicgstab<true> : batch_bicgstab<false>, kBatchBlock, 0);
-  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-  const int grid = std::max(1, std::min(nsys, ctx->num_sms * per_sm));
-  const size_t slot = batch_slot_bytes(mixed, nmax, nnzmax);
-
-  Arena sizing;
-  sizing.take<unsigned>(64);
-  sizing.take<BatchSys>(nsys);
-  sizing.take<int>(nsys);
-  sizing.take<BatchOut>(nsys);
-  sizing.take<char>(slot * grid);
-  gsk_status s = ctx->reserve(sizing.off);
-  if (s != GSK_OK) return s;
-  Arena ar{(char*)ctx->ws, ctx->ws_bytes, 0};
-  unsigned* queue = ar.take<unsigned>(64);
-  BatchSys* dsys = ar.take<BatchSys>(nsys);
-  int* dorder = ar.take<int>(nsys);
-  BatchOut* dout = ar.take<BatchOut>(nsys);
-  char* scratch = ar.take<char>(slot * grid);
-
-  cudaStream_t st = (cudaStream_t)stream;
-  GSK_CK(cudaEventRecord(ctx->ev0, st));
-  GSK_CK(cudaMemsetAsync(queue, 0, sizeof(unsigned), st));
-  GSK_CK(cudaMemcpyAsync(dsys, hs.data(), sizeof(BatchSys) * nsys, cudaMemcpyHostToDevice, st));
-  GSK_CK(cudaMemcpyAsync(dorder, order.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
-  BatchParams P{dsys, dorder, nsys, queue, dout, scratch, (long long)slot, tol, opts.inner_tol,
-                1e-16 * DBL_EPSILON, opts.maxit, opts.refresh,
-                opts.inner_maxit > 0 ? opts.inner_maxit : kBatchInnerMaxit, opts.metric == GSK_METRIC_PLAIN ? 1 : 0};
-  if (mixed) batch_bicgstab<true><<<grid, kBatchBlock, 0, st>>>(P);
-  else batch_bicgstab<false><<<grid, kBatchBlock, 0, st>>>(P);
-  GSK_CK(cudaGetLastError());
-  GSK_CK(cudaEventRecord(ctx->ev1, st));
-  if (!infos && !status) return GSK_OK;
-  std::vector<BatchOut> ho(nsys);
-  GSK_CK(cudaMemcpyAsync(ho.data(), dout, sizeof(BatchOut) * nsys, cudaMemcpyDeviceToHost, st));
-  GSK_CK(cudaStreamSynchronize(st));
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+  if (solver == 0 && mixed && !small.empty())
+    return ctx->fail(GSK_ERR_ARG, "the one-block GMRES is FP64: mixed precision only with batch_large_n routing");
   gsk_status worst = GSK_OK;
-  for (int i = 0; i < nsys; ++i) {
-    if (infos) infos[i] = gsk_info{ho[i].iters, 0, ho[i].refreshes, ho[i].refinements, ho[i].conv, ho[i].relres_true,
-                                   ho[i].relres_rec, ms};
-    if (status) status[i] = ho[i].status;
-    if (ho[i].status != GSK_OK && worst == GSK_OK) worst = (gsk_status)ho[i].status;
+  cudaStream_t st = (cudaStream_t)stream;
+  // large systems: the grid-wide path, one after the other
+  for (int i : large) {
+    gsk_info inf = {};
+    gsk_status si = GSK_OK;
+    if (!(hs[i].p != hs[i].p)) si = gs_scale(ctx, const_cast<gsk_csr*>(&A[i]), b[i], hs[i].p, nullptr, stream);
+    if (si == GSK_OK)
+      si = solver == 0 ? gmres_solve(ctx, &A[i], b[i], x[i], mvec[i], tol, &opts, &inf, stream)
+                       : bicgstab_solve(ctx, &A[i], b[i], x[i], tol, &opts, &inf, stream);
+    if (infos) infos[i] = inf;
+    if (status) status[i] = si;
+    if (si != GSK_OK && worst == GSK_OK) worst = si;
+  }
+  if (!small.empty()) {
+    const int ns = (int)small.size();
+    // largest systems first
+    std::stable_sort(small.begin(), small.end(), [&](int a, int c) { return hs[a].nnz > hs[c].nnz; });
+    int per_sm = BS == 128 ? batch_blocks_per_sm<128>(solver, mixed)
+                           : (BS == 256 ? batch_blocks_per_sm<256>(solver, mixed) : batch_blocks_per_sm<512>(solver, mixed));
+    const int grid = std::max(1, std::min(ns, ctx->num_sms * per_sm));
+    const size_t slot = solver == 0 ? batch_gmres_slot_bytes(nmax, mmax) : batch_slot_bytes(mixed, nmax, nnzmax);
+    Arena sizing;
+    sizing.take<unsigned>(64);
+    sizing.take<BatchSys>(nsys);
+    sizing.take<int>(ns);
+    sizing.take<int>(nsys);
+    sizing.take<BatchOut>(nsys);
+    sizing.take<char>(slot * grid);
+    gsk_status s = ctx->reserve(sizing.off);
+    if (s != GSK_OK) return s;
+    Arena ar{(char*)ctx->ws, ctx->ws_bytes, 0};
+    unsigned* queue = ar.take<unsigned>(64);
+    BatchSys* dsys = ar.take<BatchSys>(nsys);
+    int* dorder = ar.take<int>(ns);
+    int* dm = ar.take<int>(nsys);
+    BatchOut* dout = ar.take<BatchOut>(nsys);
+    char* scratch = ar.take<char>(slot * grid);
+    GSK_CK(cudaEventRecord(ctx->ev0, st));
+    GSK_CK(cudaMemsetAsync(queue, 0, sizeof(unsigned), st));
+    GSK_CK(cudaMemcpyAsync(dsys, hs.data(), sizeof(BatchSys) * nsys, cudaMemcpyHostToDevice, st));
+    GSK_CK(cudaMemcpyAsync(dorder, small.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+    if (solver == 0) GSK_CK(cudaMemcpyAsync(dm, mvec, sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+    BatchParams P{dsys, dorder, solver == 0 ? dm : nullptr, ns, queue, dout, scratch, (long long)slot, tol,
+                  opts.inner_tol, 1e-16 * DBL_EPSILON, opts.maxit, opts.refresh,
+                  opts.inner_maxit > 0 ? opts.inner_maxit : kBatchInnerMaxit, opts.metric == GSK_METRIC_PLAIN ? 1 : 0};
+    if (BS == 128) batch_launch<128>(solver, mixed, grid, P, st);
+    else if (BS == 256) batch_launch<256>(solver, mixed, grid, P, st);
+    else batch_launch<512>(solver, mixed, grid, P, st);
+    GSK_CK(cudaGetLastError());
+    GSK_CK(cudaEventRecord(ctx->ev1, st));
+    if (infos || status) {
+      std::vector<BatchOut> ho(nsys);
+      GSK_CK(cudaMemcpyAsync(ho.data(), dout, sizeof(BatchOut) * nsys, cudaMemcpyDeviceToHost, st));
+      GSK_CK(cudaStreamSynchronize(st));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+      for (int i : small) {
+        if (infos) infos[i] = gsk_info{ho[i].iters, ho[i].restarts, ho[i].refreshes, ho[i].refinements, ho[i].conv,
+                                       ho[i].relres_true, ho[i].relres_rec, ms};
+        if (status) status[i] = ho[i].status;
+        if (ho[i].status != GSK_OK && worst == GSK_OK) worst = (gsk_status)ho[i].status;
+      }
+    }
   }
   if (worst != GSK_OK) return ctx->fail(worst, "at least one system of the batch failed (see status[])");
   return GSK_OK;
+}
+
+}  // namespace gsk
+
+extern "C" gsk_status bicgstab_solve_batched(gsk_ctx* ctx, int nsys, const gsk_csr* A, void* const* b,
+                                             void* const* x, const double* p, double tol, const gsk_opts* opts,
+                                             gsk_info* infos, int32_t* status, void* stream) {
+  return gsk::batch_solve(ctx, 1, nsys, A, b, x, p, nullptr, tol, opts, infos, status, stream);
+}
+
+extern "C" gsk_status gmres_solve_batched(gsk_ctx* ctx, int nsys, const gsk_csr* A, void* const* b, void* const* x,
+                                          const double* p, const int* m, double tol, const gsk_opts* opts,
+                                          gsk_info* infos, int32_t* status, void* stream) {
+  return gsk::batch_solve(ctx, 0, nsys, A, b, x, p, m, tol, opts, infos, status, stream);
 }
