@@ -583,10 +583,10 @@ def profile_pass(g, ctx, A, val0, b, b0, s):
 
 
 # ---------------------------------------------------------------- CPU oracle
-def cpu_sample(s, bcg_iters=60, gm_cycles=2):
+def cpu_sample(s, bcg_iters=80, gm_cycles=3):
     """The CPU oracle (one thread) on a bounded sample of the workload: GS(2),
-    bcg_iters Bi-CGSTAB iterations and gm_cycles full GMRES(30) cycles (about
-    10 s of CPU work), scaled to a whole solve by the oracle's own iteration
+    bcg_iters Bi-CGSTAB iterations and gm_cycles full GMRES(30) cycles (10-15 s
+    of CPU work), scaled to a whole solve by the oracle's own iteration
     counts for this workload (tests/golden/c2_oracle_counts.json)."""
     import oracle
 
