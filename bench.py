@@ -347,6 +347,7 @@ def run_gpu(args):
         extra["batched"] = batched_pass(g, args)
         extra["c3_256"] = c3_pass(g)
         extra["serving"] = serving_pass(args)
+        extra["spectrum"] = spectrum_pass(g, ctx, A, val0, b, b0, s)
 
     if rank == 0:
         i1, i2 = infos[-1]
@@ -365,6 +366,29 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def spectrum_pass(g, ctx, A, val0, b, b0, s, m=64):
+    """Ritz values of 64 Arnoldi steps (gsk_arnoldi) on the GS(2)-scaled
+    workload: the eigenvalue diagnostic at a size no dense solver takes."""
+    import time
+
+    import numpy as np
+    import torch
+
+    A.val.copy_(val0)
+    b.copy_(b0)
+    g.gs_scale(A, b, p=2.0, ctx=ctx)
+    v0 = torch.as_tensor(np.random.default_rng(0).normal(size=s.n), device=A.val.device)
+    g.arnoldi(A, v0, 4, ctx=ctx)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H, k = g.arnoldi(A, v0, m, ctx=ctx)
+    sec = time.perf_counter() - t0
+    ritz = np.linalg.eigvals(H[:k, :k])
+    return {"steps": k, "ms": 1e3 * sec, "us_per_step": 1e6 * sec / max(k, 1),
+            "ritz_lambda_max": float(np.abs(ritz).max()), "ritz_lambda_min": float(np.abs(ritz).min()),
+            "note": "one host synchronisation per step"}
 
 
 def mixed_pass(g, ctx, A, val0, b, b0, x1, x2, args):

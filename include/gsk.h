@@ -263,6 +263,28 @@ gsk_status gmres_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, i
                        const gsk_opts* opts, gsk_info* info, void* stream);
 
 /*
+ * gsk_arnoldi -- the Arnoldi process of GMRES (Sec. 2: classical Gram-Schmidt
+ * applied twice) on A from v0, for the eigenvalue-distribution diagnostic of
+ * Sec. 3 (Tables 1b and 4a): the Ritz values, eigenvalues of the leading
+ * k x k block of H, approximate A's extreme eigenvalues.
+ *   A      FP64 CSR (device); apply gs_scale first to study the scaled matrix
+ *   v0     device [n] FP64, the starting vector (normalised here; not modified)
+ *   m      number of steps, 1..64
+ *   H      host [(m+1) * m] FP64, column-major with leading dimension m+1:
+ *          A V_k = V_{k+1} H(0:k+1, 0:k) for the orthonormal basis V; entries
+ *          beyond the k steps taken are zero
+ *   steps  host: k = m, or fewer when the Krylov space becomes invariant
+ *          (h_{k+1,k} <= 1e-14 ||A v_k||, the breakdown rule of gmres_solve);
+ *          0 when v0 = 0
+ * Runs the solver's kernels from a host loop (one synchronisation per step)
+ * and synchronises `stream` before returning.  GSK_ERR_ARG for a non-FP64
+ * matrix, m outside 1..64 or a NULL pointer; GSK_ERR_NONFINITE when v0 or A
+ * v_j is not finite.
+ */
+gsk_status gsk_arnoldi(gsk_ctx* ctx, const gsk_csr* A, const double* v0, int m, double* H, int* steps,
+                       void* stream);
+
+/*
  * bicgstab_solve -- Bi-CGSTAB (Sec. 2; van der Vorst 1992) with breakdown
  * tolerance 1e-16 * DBL_EPSILON relative to the vector norms (Sec. 2.2) and
  * true-residual confirmation.  Arguments as for gmres_solve.
@@ -286,9 +308,7 @@ gsk_status bicgstab_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x
  *           solves (relative tolerance inner_tol, at most inner_maxit
  *           iterations each, 40 when 0) in FP64 refinement; a system whose
  *           refinement step gains less than 10x in the FP64 metric is
- *           finished by FP64 Bi-CGSTAB from its current x
- *   infos   host array [nsys] or NULL; status host array [nsys] or NULL
- *           (per-system gsk_status: GSK_ERR_ZERO_ROW / NONFINITE / ARG).
+ *           finished by FP64 Bi-CGSTAB from its current x;
  *           batch_block (threads per block: 128, 256, 512; 0 = 256) and
  *           batch_large_n (systems with more rows are solved first, one at
  *           a time, by gs_scale and the grid-wide solver with the same

@@ -280,14 +280,18 @@ static void arnoldi_step(int n, const int* rp, const int* ci, const double* va, 
 
 /* k Arnoldi steps from v0 (normalised here), exposing V (n x (k+1)) and the
  * Hessenberg matrix H ((k+1) x k, column-major) built by arnoldi_step.
- * Returns the number of steps completed (fewer than k at exact breakdown). */
+ * Returns the number of steps completed: fewer than k when the Krylov space
+ * is numerically invariant (h_{j+1,j} <= 1e-14 ||A v_j||, GMRES's rule), 0
+ * for v0 = 0.  The eigenvalues of the leading square block are the Ritz
+ * values used for the eigenvalue analysis of Sec. 3. */
 int or_arnoldi(int n, const int* rp, const int* ci, const double* va,
                const double* v0, int k, double* V, double* H) {
   double* h2 = (double*)malloc(sizeof(double) * (k + 1));
   if (!h2) return -1;
   double beta = sqrt(dot(n, v0, v0));
-  for (int i = 0; i < n; ++i) V[i] = v0[i] / beta;
   memset(H, 0, sizeof(double) * (size_t)(k + 1) * k);
+  if (beta == 0.0) { free(h2); return 0; }
+  for (int i = 0; i < n; ++i) V[i] = v0[i] / beta;
   int done = 0;
   for (int j = 0; j < k; ++j) {
     double awn;
@@ -295,7 +299,7 @@ int or_arnoldi(int n, const int* rp, const int* ci, const double* va,
     double* w = V + (size_t)(j + 1) * n;
     arnoldi_step(n, rp, ci, va, NULL, V, j, hcol, w, h2, &awn, NULL);
     done = j + 1;
-    if (hcol[j + 1] == 0.0) break;
+    if (hcol[j + 1] <= 1e-14 * awn) break;
     for (int i = 0; i < n; ++i) w[i] /= hcol[j + 1];
   }
   free(h2);

@@ -88,6 +88,8 @@ SIGNATURES = {
     "gsk_spmv": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gmres_solve": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                      C.POINTER(OptsC), C.POINTER(InfoC), C.c_void_p], C.c_int),
+    "gsk_arnoldi": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
+                     C.c_void_p], C.c_int),
     "bicgstab_solve": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_double,
                         C.POINTER(OptsC), C.POINTER(InfoC), C.c_void_p], C.c_int),
     "gsk_workspace_bytes": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)], C.c_int),
@@ -338,6 +340,23 @@ def gmres_solve(A: Csr, b, x, m: int = 30, tol: float = 1e-8, options: OptsC | N
     ctx.check(lib().gmres_solve(ctx.handle, C.byref(Ac), _ptr(b), _ptr(x), int(m), float(tol), C.byref(o),
                                 C.byref(info) if sync else None, _stream_ptr(stream)))
     return info.as_dict() if sync else None
+
+
+def arnoldi(A: Csr, v0, m: int, ctx: Context | None = None, stream=None):
+    """m steps of GMRES's Arnoldi process (CGS2, Sec. 2) on the device from
+    v0; returns (H, k): H the (k+1) x k Hessenberg matrix (numpy FP64) with
+    A V_k = V_{k+1} H, k <= m the steps taken (fewer at an invariant
+    subspace).  The eigenvalues of H[:k, :k] are the Ritz values."""
+    import numpy as np
+
+    ctx = ctx or default_context(A.val.device.index or 0)
+    Ac = A.c()
+    H = np.zeros((m, m + 1), dtype=np.float64)  # column-major (m+1) x m, transposed view
+    k = C.c_int(0)
+    ctx.check(lib().gsk_arnoldi(ctx.handle, C.byref(Ac), _ptr(v0), int(m),
+                                H.ctypes.data_as(C.POINTER(C.c_double)), C.byref(k), _stream_ptr(stream)))
+    k = k.value
+    return np.ascontiguousarray(H.T[: k + 1, :k]), k
 
 
 def bicgstab_solve(A: Csr, b, x, tol: float = 1e-8, options: OptsC | None = None, ctx: Context | None = None,

@@ -4,6 +4,8 @@
 #include "graph.hpp"
 #include "ilu.cuh"
 
+#include <cmath>
+
 namespace gsk {
 
 // ------------------------------------------------------------------ host
@@ -15,6 +17,7 @@ constexpr int kGmIluV = 1000, kGmIluU = 1001, kGmXadd = 1002;
 struct GmPlan {
   const gsk_ilu0* pre = nullptr;
   double *zbuf = nullptr, *ubuf = nullptr;
+  double* xzero = nullptr;  // Arnoldi mode: x0 = 0, so that r0 = v0
   int g_tile, g_gx, wmode, KP, nclass;
   int g_gd[kGmClasses], g_gb[kGmClasses], g_gc[kGmClasses];
   GmArgs<double> a;
@@ -152,7 +155,7 @@ static gsk_status gm_record(gsk_ctx* ctx, GmPlan& P, cudaGraphExec_t* exec_out) 
 }
 
 static gsk_status gm_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, int m, double tol,
-                             const gsk_opts& opts, GmPlan& P) {
+                             const gsk_opts& opts, GmPlan& P, bool arnoldi = false) {
   if (A->dtype != GSK_F64) return ctx->fail(GSK_ERR_ARG, "the FP64 solver needs an FP64 matrix");
   if (!(tol >= 0.0) || opts.maxit < 0) return ctx->fail(GSK_ERR_ARG, "bad tol/maxit");
   if (A->n > 0 && (!b || !x)) return ctx->fail(GSK_ERR_ARG, "NULL b or x");
@@ -190,6 +193,8 @@ static gsk_status gm_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, void
     P.wbuf = P.wmode == 0 ? ar.take<double>(n) : nullptr;
     P.zbuf = P.pre ? ar.take<double>(n) : nullptr;
     P.ubuf = P.pre ? ar.take<double>(n) : nullptr;
+    P.xzero = arnoldi ? ar.take<double>(n) : nullptr;
+    a.Hraw = arnoldi ? ar.take<double>((size_t)(m + 1) * m) : nullptr;
   };
   Arena sizing;
   layout(sizing);
@@ -205,7 +210,7 @@ static gsk_status gm_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, void
   a.colidx = A->colidx;
   a.val = (const double*)A->val;
   a.b = (const double*)b;
-  a.x = (double*)x;
+  a.x = arnoldi ? P.xzero : (double*)x;
   a.w = P.wmode == 0 ? P.wbuf : (P.wmode == 2 ? opts.weights : nullptr);
   a.in_graph = 0;
   a.vec_ok = ((uintptr_t)x % 16) == 0;
@@ -273,9 +278,61 @@ gsk_status gm_profile(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, in
   return err_bits_status(ctx, bits);
 }
 
+// The Arnoldi process alone: init (r0 = v0 - A 0 = v0) and m steps of the
+// solver's basis kernels from a host loop, one readback per step; gm_gc
+// records the unrotated Hessenberg columns.  The step loop ends where a GMRES
+// cycle would (k = m or breakdown): tol 0 never ends it, maxit = m.
+static gsk_status gm_arnoldi(gsk_ctx* ctx, const gsk_csr* A, const double* v0, int m, double* H, int* steps,
+                             cudaStream_t st) {
+  gsk_opts opts;
+  gsk_opts_default(&opts);
+  opts.metric = GSK_METRIC_PLAIN;
+  opts.maxit = m;
+  GmPlan P;
+  gsk_status s = gm_prepare(ctx, A, v0, (void*)v0, m, 0.0, opts, P, true);
+  if (s != GSK_OK) return s;
+  const size_t hbytes = sizeof(double) * (size_t)(m + 1) * m;
+  std::memset(H, 0, hbytes);
+  *steps = 0;
+  if (A->n == 0) return GSK_OK;
+  if ((s = gm_upload(ctx, P, st)) != GSK_OK) return s;
+  GSK_CK(cudaMemsetAsync(P.xzero, 0, sizeof(double) * (size_t)A->n, st));
+  GSK_CK(cudaMemsetAsync(P.a.Hraw, 0, hbytes, st));
+  gm_launch(ctx, P, kKGmInit, st);
+  GSK_CK(cudaGetLastError());
+  GmState S;
+  int bits = 0;
+  if ((s = gm_readback(ctx, P, st, S, bits)) != GSK_OK) return s;
+  while (!S.stop && !bits) {
+    const int c = gm_kclass(S.j + 1);
+    gm_launch(ctx, P, kKGmGa, st);
+    for (int k : {kKGmGd, kKGmGb, kKGmGc}) gm_launch_cgs(P, k, c, st);
+    GSK_CK(cudaGetLastError());
+    if ((s = gm_readback(ctx, P, st, S, bits)) != GSK_OK) return s;
+    if (!S.cont) break;
+  }
+  if ((s = err_bits_status(ctx, bits)) != GSK_OK) return s;
+  if (!S.stop) *steps = S.kcols;
+  GSK_CK(cudaMemcpyAsync(H, P.a.Hraw, hbytes, cudaMemcpyDeviceToHost, st));
+  GSK_CK(cudaStreamSynchronize(st));
+  for (size_t i = 0; i < (size_t)(m + 1) * m; ++i)
+    if (!std::isfinite(H[i])) return ctx->fail(GSK_ERR_NONFINITE, "non-finite Hessenberg entry");
+  return GSK_OK;
+}
+
 }  // namespace gsk
 
 using namespace gsk;
+
+extern "C" gsk_status gsk_arnoldi(gsk_ctx* ctx, const gsk_csr* A, const double* v0, int m, double* H, int* steps,
+                                  void* stream) {
+  if (!ctx) return GSK_ERR_ARG;
+  gsk_status s = check_csr(ctx, A);
+  if (s != GSK_OK) return s;
+  if (m < 1 || m > kMaxM) return ctx->fail(GSK_ERR_ARG, "m must be in 1..64");
+  if (!H || !steps || (A->n > 0 && !v0)) return ctx->fail(GSK_ERR_ARG, "NULL v0, H or steps");
+  return gm_arnoldi(ctx, A, v0, m, H, steps, (cudaStream_t)stream);
+}
 
 extern "C" gsk_status gmres_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, int m, double tol,
                                   const gsk_opts* opts_in, gsk_info* info, void* stream) {

@@ -67,6 +67,9 @@ struct GmArgs {
   // to u_out (then x += M^-1 u_out); both null without a preconditioner
   const T* zin;
   T* u_out;
+  // Arnoldi mode: gm_gc also stores each Hessenberg column before the Givens
+  // rotations ((m+1) x m, column-major); null in the solvers
+  double* Hraw;
   // unrolled cycle: the graph holds the m steps of a cycle as a chain (step j
   // with the basis kernels of class gm_kclass(j + 1)) instead of an inner
   // WHILE node; once the cycle has ended (S->cont == 0) the remaining steps'
@@ -390,6 +393,11 @@ __global__ void __launch_bounds__(kBlock) gm_gc(GmArgs<T> a) {
     double* hcol = a.H + (long long)j * ld;
     for (int c = 0; c <= j; ++c) hcol[c] = a.h1[c] + a.h2[c];
     const double hnext = sqrt(tot[0]);
+    if (a.Hraw) {
+      double* hr = a.Hraw + (long long)j * ld;
+      for (int c = 0; c <= j; ++c) hr[c] = hcol[c];
+      hr[j + 1] = hnext;
+    }
     // ||A v_j||^2 = ||h1 + h2||^2 + hnext^2 (w's parts along the orthonormal
     // basis and orthogonal to it)
     double aw2 = hnext * hnext;

@@ -1,6 +1,6 @@
 """Runs the paper's experiments without ILUT on the GPU path.
 
-    python -m paper_0812_2769_gb300.reproduce [--tables 1,1a,1v,4,limit] [--grid4 80]
+    python -m paper_0812_2769_gb300.reproduce [--tables 1,1a,1v,4,limit,1b,4a] [--grid4 80]
 
 Problem 1 (Sec. 3): 128x128, b = A (1,...,1)^T; Table 1 (a = b = 1e3 on
 (1/4,3/4)^2, else 1), the a = b = 1e4 variant Sec. 3 describes, Table 1a
@@ -18,6 +18,13 @@ Each solve runs through the library: the system is copied to the device,
 gs_scale applies GS(2) there, and gmres_solve / bicgstab_solve run the whole
 iteration as one graph launch.  Output: one markdown table per paper table,
 iterations (or "no conv." with the relative residual reached) per tolerance.
+
+Tables 1b and 4a (eigenvalue information): Problem 1 on a 40x40 grid and
+Problem 4 (D = 1e4) on 12x12x12, the original matrix, the matrix after GS(2)
+(applied on the device by gs_scale) and the continuous-coefficient variant;
+all eigenvalues by the host's dense eigensolver (spectrum.dense_eigenvalues)
+beside the largest Ritz value of 64 Arnoldi steps on the device
+(spectrum.ritz_values) and the paper's printed values.
 """
 from __future__ import annotations
 
@@ -81,11 +88,72 @@ def solve_case(g, s, solver: str, scaled, tol: float, m: int = 10, ctx=None, pre
     return info["conv"] == 0, int(info["iters"]), float(info["relres_true"]), ms
 
 
+# The paper's printed eigenvalue information: (lambda_min, lambda_max,
+# ratio, count in the first interval (1b) / around the origin (4a)).
+PAPER_EIGEN = {
+    "1b": {"original": (1.87e-2, 7.96e3, 4.25e5, 1126), "gs": (7.07e-6, 1.78, 2.52e5, 4),
+           "continuous": (11.7, 8.00e3, 6.81e2, 8)},  # Table 1b
+    "4a": {"original": (1.45e-2, 2.93e3, 2.02e5, 1131), "gs": (2.41e-6, 1.00, 4.16e5, 25),
+           "continuous": (3.61, 6.18e4, 1.71e4, 42)},  # Table 4a
+}
+
+
+def eigen_case(g, s, scaled: bool, ritz_steps: int = 64, ctx=None):
+    """Dense eigenvalue summary (host LAPACK) of the system's matrix, GS(2)
+    applied on the device first when scaled, and the largest Ritz value
+    modulus of ritz_steps Arnoldi steps on the device."""
+    import torch
+
+    from . import spectrum
+
+    A = g.Csr.from_host(s.rowptr, s.colidx, s.val, device="cuda")
+    if scaled:
+        g.gs_scale(A, torch.as_tensor(s.b, device="cuda"), p=2.0, ctx=ctx)
+    d = spectrum.summary(spectrum.dense_eigenvalues(A))
+    ritz, _, k = spectrum.ritz_values(A, m=min(ritz_steps, s.n), ctx=ctx)
+    d["ritz_lambda_max"] = float(np.abs(ritz).max()) if k else 0.0
+    d["ritz_steps"] = k
+    return d
+
+
+def _eigen_systems(which: str):
+    from problems import configs
+
+    if which == "1b":
+        return [("original", configs.p1(40)), ("gs", configs.p1(40)),
+                ("continuous", configs.p1(40, continuous=1000.0))]
+    if which == "4a":
+        return [("original", configs.p4(12, D=1.0e4)), ("gs", configs.p4(12, D=1.0e4)),
+                ("continuous", configs.p4(12, D=1.0e4, continuous=True))]
+    raise ValueError(which)
+
+
+def run_eigen(which: str, out=print, ctx=None):
+    import paper_0812_2769_gb300 as g
+
+    col = "first interval" if which == "1b" else "around x = 0"
+    out(f"\n### Table {which}: eigenvalue information (paper's values in brackets)\n")
+    out(f"| matrix | n | lambda_min | lambda_max | ratio | {col} | largest Ritz value, 64 steps |")
+    out("|---|---|---|---|---|---|---|")
+    res = {}
+    for label, s in _eigen_systems(which):
+        d = eigen_case(g, s, label == "gs", ctx=ctx)
+        res[label] = d
+        pmin, pmax, prat, pcnt = PAPER_EIGEN[which][label]
+        cnt = d["first_interval"] if which == "1b" else d["origin_interval"]
+        out(f"| {label} | {s.n} | {d['lambda_min']:.3g} ({pmin:.3g}) | {d['lambda_max']:.3g} ({pmax:.3g}) | "
+            f"{d['ratio']:.3g} ({prat:.3g}) | {cnt} ({pcnt}) | {d['ritz_lambda_max']:.4g} |")
+    return res
+
+
 def run(tables, grid4: int = 80, out=print):
     import paper_0812_2769_gb300 as g
 
     results = {}
     for t in tables:
+        if t in PAPER_EIGEN:
+            results[t] = run_eigen(t, out=out)
+            continue
         for label, s in _systems(t, grid4):
             out(f"\n### Table {t}: {s.meta.get('name', '')}, {label} (n = {s.n})\n")
             out("| method | rel-res 1e-4 | rel-res 1e-7 | rel-res 1e-10 |")
@@ -106,7 +174,7 @@ def run(tables, grid4: int = 80, out=print):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--tables", default="1,1v,1a,4,limit")
+    ap.add_argument("--tables", default="1,1v,1a,4,limit,1b,4a")
     ap.add_argument("--grid4", type=int, default=80, help="grid side of Problem 4's Table 4 (paper: 80)")
     args = ap.parse_args(argv)
     np.set_printoptions(precision=3)

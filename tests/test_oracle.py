@@ -299,6 +299,53 @@ def test_arnoldi_relation_and_orthogonality():
     assert np.all(np.diag(H, -1) > 0)
 
 
+@pytest.mark.parametrize("k", [1, 4, 7])
+def test_arnoldi_finite_termination_gives_the_eigenvalues(k):
+    """A diagonal matrix with k distinct eigenvalues has a grade-k Krylov space:
+    the Arnoldi process stops after exactly k steps (h_{k+1,k} ~ rounding), and
+    the Ritz values of H(0:k, 0:k) are those k eigenvalues."""
+    n = 90
+    vals = np.array([0.5 + 1.3 * j for j in range(k)])
+    rp, ci, va = _diag_csr(vals[np.arange(n) % k])
+    v0 = np.random.default_rng(7).uniform(1, 2, n)
+    _, H, steps = oracle.arnoldi(rp, ci, va, v0, 12)
+    assert steps == k
+    ritz = np.sort(np.linalg.eigvals(H[:k, :k]).real)
+    assert np.allclose(ritz, vals, rtol=1e-12)
+    assert np.all(H[:, k:] == 0.0)
+
+
+def test_arnoldi_full_length_ritz_values_are_the_eigenvalues():
+    """n steps on an n x n matrix: H(0:n, 0:n) = V^T A V is similar to A, so
+    its eigenvalues equal LAPACK's eigenvalues of A."""
+    A, rp, ci, va = _random_csr(30, 11, density=0.3)
+    v0 = np.random.default_rng(12).normal(size=30)
+    _, H, steps = oracle.arnoldi(rp, ci, va, v0, 30)
+    assert steps == 30
+    ea = np.sort_complex(np.linalg.eigvals(A))
+    eh = np.sort_complex(np.linalg.eigvals(H[:30, :30]))
+    assert np.allclose(ea, eh, rtol=1e-9, atol=1e-10 * np.abs(ea).max())
+
+
+def test_arnoldi_symmetric_matrix_gives_a_symmetric_tridiagonal_h():
+    """For symmetric A, H = V^T A V is symmetric and so tridiagonal (Lanczos)."""
+    A, rp, ci, va = _random_csr(40, 13, density=0.2)
+    As = A + A.T
+    rows, cols = np.nonzero(As)
+    rp = np.searchsorted(rows, np.arange(41)).astype(np.int32)
+    _, H, steps = oracle.arnoldi(rp, cols.astype(np.int32), As[rows, cols], np.ones(40), 10)
+    T = H[:10, :10]
+    scale = np.abs(T).max()
+    assert np.abs(np.triu(T, 2)).max() <= 1e-12 * scale
+    assert np.allclose(np.diag(T, 1), np.diag(T, -1), rtol=1e-10)
+
+
+def test_arnoldi_zero_start_takes_no_step():
+    s = configs.c1(6)
+    _, H, steps = oracle.arnoldi(s.rowptr, s.colidx, s.val, np.zeros(s.n), 5)
+    assert steps == 0 and np.all(H == 0.0)
+
+
 # ------------------------------------------------------------------ GMRES
 def _diag_csr(d):
     n = len(d)
