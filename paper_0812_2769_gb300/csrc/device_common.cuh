@@ -73,10 +73,10 @@ __device__ __forceinline__ T warp_allsum(T v) {
 }
 
 // Block-wide sum of nv per-thread values held in shared memory as
-// tab[k * BLOCK + t] (the table is consumed).  Result in res[k] (shared),
-// valid after the call.  Tree as in block_sum.
-template <int BLOCK>
-__device__ __forceinline__ void block_sum_table(double* tab, int nv, double* res) {
+// tab[k * BLOCK + t] (the table is consumed), added in the table's type.
+// Result in res[k] (shared), valid after the call.  Tree as in block_sum.
+template <int BLOCK, typename TT>
+__device__ __forceinline__ void block_sum_table(TT* tab, int nv, double* res) {
   __syncthreads();
 #pragma unroll
   for (int s = BLOCK / 2; s >= 32; s >>= 1) {
@@ -86,8 +86,8 @@ __device__ __forceinline__ void block_sum_table(double* tab, int nv, double* res
   }
   // the remaining 32 partial sums of each value: one warp per value
   for (int k = warp_id(); k < nv; k += BLOCK / 32) {
-    const double t = warp_allsum(tab[k * BLOCK + lane_id()]);
-    if (lane_id() == 0) res[k] = t;
+    const TT t = warp_allsum(tab[k * BLOCK + lane_id()]);
+    if (lane_id() == 0) res[k] = (double)t;
   }
   __syncthreads();
 }

@@ -96,18 +96,22 @@ __device__ __forceinline__ void gm_set_cond(const GmArgs<T>& a, cudaGraphConditi
 __device__ __forceinline__ double gm_wgt(const double* w, bool wid, int i) { return wid ? 1.0 : __ldg(w + i); }
 
 // Block sum of NV register accumulators (only the first nv are needed), in
-// chunks of 16 rows of a [min(NV, 16)][kBlock] shared table.
+// chunks of 16 rows of a [min(NV, 16)][kBlock] shared table, added in the
+// accumulators' type: FP64 for the FP64 solver; FP32 for the FP32 inner
+// solves, whose per-thread sums are FP32 already (an FP64 tree there would
+// spend the scarce FP64 pipe on k x 255 additions per block).  The block
+// totals go on to the grid-wide sum in FP64.
 template <int NV>
 __host__ __device__ constexpr int chunk_rows() { return NV < 16 ? NV : 16; }
 template <int NV, typename A>
-__device__ __forceinline__ void block_sum_chunked(const A (&v)[NV], int nv, double* table, double* res) {
+__device__ __forceinline__ void block_sum_chunked(const A (&v)[NV], int nv, A* table, double* res) {
 #pragma unroll
   for (int c0 = 0; c0 < NV; c0 += 16) {
     if (c0 < nv) {
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < 16; ++q)
-        if (c0 + q < NV) table[q * kBlock + threadIdx.x] = (double)v[c0 + q];
+        if (c0 + q < NV) table[q * kBlock + threadIdx.x] = v[c0 + q];
       block_sum_table<kBlock>(table, min(16, nv - c0), res + c0);
     }
   }
@@ -256,7 +260,8 @@ template <typename T, int KP>
 __global__ void __launch_bounds__(kBlock) gm_gd(GmArgs<T> a) {
   using Acc = typename AccOf<T>::type;
   constexpr int R = Vec16<T>::R;
-  __shared__ double table[chunk_rows<KP>() * kBlock], res[KP], tot[KP];
+  __shared__ Acc table[chunk_rows<KP>() * kBlock];
+  __shared__ double res[KP], tot[KP];
   const GmState* S = a.S;
   if (a.unrolled && !S->cont) return;  // the cycle ended at an earlier step
   const int j = S->j, k = j + 1;
@@ -294,7 +299,8 @@ __global__ void __launch_bounds__(kBlock) gm_gb(GmArgs<T> a) {
   using Acc = typename AccOf<T>::type;
   constexpr int R = Vec16<T>::R;
   __shared__ Acc coef[KP];
-  __shared__ double table[chunk_rows<KP>() * kBlock], res[KP], tot[KP];
+  __shared__ Acc table[chunk_rows<KP>() * kBlock];
+  __shared__ double res[KP], tot[KP];
   const GmState* S = a.S;
   if (a.unrolled && !S->cont) return;  // the cycle ended at an earlier step
   const int j = S->j, k = j + 1;
@@ -388,39 +394,51 @@ __global__ void __launch_bounds__(kBlock) gm_gc(GmArgs<T> a) {
   }
   const double accd[1] = {(double)acc[0]};
   block_sum<1, kBlock>(accd, table, res);
-  if (grid_sum(res, 1, a.red, tot) && threadIdx.x == 0) {
-    const int ld = a.m + 1;
-    double* hcol = a.H + (long long)j * ld;
-    for (int c = 0; c <= j; ++c) hcol[c] = a.h1[c] + a.h2[c];
-    const double hnext = sqrt(tot[0]);
-    if (a.Hraw) {
-      double* hr = a.Hraw + (long long)j * ld;
-      for (int c = 0; c <= j; ++c) hr[c] = hcol[c];
-      hr[j + 1] = hnext;
+  if (!grid_sum(res, 1, a.red, tot)) return;
+  // The closing block: the Hessenberg column h1 + h2 and the earlier
+  // rotations are gathered into shared memory by all its threads at once;
+  // one thread then rotates there (a serial walk over global memory would
+  // pay a memory round trip per column).
+  __shared__ double hs[kMaxM + 2], css[kMaxM], sns[kMaxM];
+  const int ld = a.m + 1;
+  for (int c = threadIdx.x; c <= j; c += kBlock) {
+    const double h = a.h1[c] + a.h2[c];
+    hs[c] = h;
+    if (a.Hraw) a.Hraw[(long long)j * ld + c] = h;
+    if (c < j) {
+      css[c] = a.cs[c];
+      sns[c] = a.sn[c];
     }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double* hcol = a.H + (long long)j * ld;
+    const double hnext = sqrt(tot[0]);
+    if (a.Hraw) a.Hraw[(long long)j * ld + j + 1] = hnext;
     // ||A v_j||^2 = ||h1 + h2||^2 + hnext^2 (w's parts along the orthonormal
     // basis and orthogonal to it)
     double aw2 = hnext * hnext;
-    for (int c = 0; c <= j; ++c) aw2 = fma(hcol[c], hcol[c], aw2);
+    for (int c = 0; c <= j; ++c) aw2 = fma(hs[c], hs[c], aw2);
     S->aw_norm = sqrt(aw2);
     S->iters += 1;
     for (int q = 0; q < j; ++q) {
-      const double t0 = a.cs[q] * hcol[q] + a.sn[q] * hcol[q + 1];
-      const double t1 = -a.sn[q] * hcol[q] + a.cs[q] * hcol[q + 1];
-      hcol[q] = t0;
-      hcol[q + 1] = t1;
+      const double t0 = css[q] * hs[q] + sns[q] * hs[q + 1];
+      const double t1 = -sns[q] * hs[q] + css[q] * hs[q + 1];
+      hs[q] = t0;
+      hs[q + 1] = t1;
     }
-    const double rho = hypot(hcol[j], hnext);
+    const double rho = hypot(hs[j], hnext);
     double c_, s_;
     if (rho == 0.0) {
       c_ = 1.0;
       s_ = 0.0;
     } else {
-      c_ = hcol[j] / rho;
+      c_ = hs[j] / rho;
       s_ = hnext / rho;
     }
     a.cs[j] = c_;
     a.sn[j] = s_;
+    for (int q = 0; q < j; ++q) hcol[q] = hs[q];
     hcol[j] = rho;
     hcol[j + 1] = 0.0;
     const double gj = a.g[j];

@@ -231,7 +231,6 @@ __global__ void __launch_bounds__(kBlock) mx_prep_gm(MxArgs a) {
     Sg->est_hit = 0;
     Sg->est = 1.0;
     Sg->cont = 1;
-    cudaGraphSetConditional(a.h_inner, 1u);
   }
 }
 
@@ -263,6 +262,9 @@ __global__ void __launch_bounds__(kBlock) mx_update_gm(MxArgs a) {
 
 struct MxPlan {
   int solver, wmode, KP, g_tile, g_vec, g_vec2, m;
+  // inner GMRES: grids of the basis kernels per column class (as the FP64
+  // solver: the step with k columns runs the instance of class gm_kclass(k))
+  int nclass, g_gd[kGmClasses], g_gb[kGmClasses], g_gc[kGmClasses];
   MxArgs a;
   BcgArgs<float> bi;
   GmArgs<float> gi;
@@ -271,6 +273,9 @@ struct MxPlan {
   BcgState hb;
   GmState hg;
 };
+
+template <int KP>
+static void mx_grids_class(gsk_ctx* ctx, MxPlan& P, int c, int n);
 
 static gsk_status mx_prepare(gsk_ctx* ctx, int solver, const gsk_csr* A, const void* b, void* x, int m,
                              double tol, const gsk_opts& opts, MxPlan& P) {
@@ -286,9 +291,20 @@ static gsk_status mx_prepare(gsk_ctx* ctx, int solver, const gsk_csr* A, const v
   P.g_tile = ctx->spmv_grid(n);
   P.g_vec = ctx->grid_for(n, kBlock, 4);
   P.g_vec2 = ctx->occ_grid((const void*)bcg_k3<float>, (n + 3) / 4, kBlock);  // four FP32 rows per thread
-  const int g_gm = ctx->grid_for(n, kBlock, P.KP <= 16 ? 4 : 2);
   int gmax = P.g_tile;
-  for (int g : {P.g_vec, P.g_vec2, g_gm, ctx->grid_for(n, kBlock, 8)}) gmax = g > gmax ? g : gmax;
+  for (int g : {P.g_vec, P.g_vec2, ctx->grid_for(n, kBlock, 8)}) gmax = g > gmax ? g : gmax;
+  P.nclass = 0;
+  if (solver == 0) {
+    P.nclass = gm_kclass(m) + 1;
+    for (int c = 0; c < kGmClasses; ++c) P.g_gd[c] = P.g_gb[c] = P.g_gc[c] = 1;
+    mx_grids_class<4>(ctx, P, 0, n);
+    if (P.nclass > 1) mx_grids_class<8>(ctx, P, 1, n);
+    if (P.nclass > 2) mx_grids_class<16>(ctx, P, 2, n);
+    if (P.nclass > 3) mx_grids_class<32>(ctx, P, 3, n);
+    if (P.nclass > 4) mx_grids_class<64>(ctx, P, 4, n);
+    for (int c = 0; c < P.nclass; ++c)
+      for (int g : {P.g_gd[c], P.g_gb[c], P.g_gc[c]}) gmax = g > gmax ? g : gmax;
+  }
   const long long ldv = ((long long)n + 63) / 64 * 64;
   MxArgs& a = P.a;
   std::memset(&a, 0, sizeof(a));
@@ -410,6 +426,7 @@ static gsk_status mx_prepare(gsk_ctx* ctx, int solver, const gsk_csr* A, const v
     gi.cnt = a.cnt;
     gi.err = a.err;
     gi.in_graph = 1;
+    gi.unrolled = 1;
     std::memset(&P.hg, 0, sizeof(P.hg));
     P.hg.tau = opts.inner_tol;
     P.hg.tol = opts.inner_tol;
@@ -424,10 +441,6 @@ static gsk_status mx_prepare(gsk_ctx* ctx, int solver, const gsk_csr* A, const v
 template <int KP>
 static void mx_launch_gm(MxPlan& P, int which, cudaStream_t s) {
   switch (which) {
-    case 0: gm_ga<float><<<P.g_tile, kBlock, 0, s>>>(P.gi); break;
-    case 1: gm_gd<float, KP><<<P.g_vec, kBlock, 0, s>>>(P.gi); break;
-    case 2: gm_gb<float, KP><<<P.g_vec, kBlock, 0, s>>>(P.gi); break;
-    case 3: gm_gc<float, KP><<<P.g_vec, kBlock, 0, s>>>(P.gi); break;
     case 4: gm_gy<float><<<1, 32, 0, s>>>(P.gi); break;
     case 5: mx_update_gm<KP><<<P.g_vec, kBlock, 0, s>>>(P.a); break;
   }
@@ -437,6 +450,38 @@ static void mx_gm(MxPlan& P, int which, cudaStream_t s) {
   if (P.KP == 16) mx_launch_gm<16>(P, which, s);
   else if (P.KP == 32) mx_launch_gm<32>(P, which, s);
   else mx_launch_gm<64>(P, which, s);
+}
+
+// One inner Arnoldi step with k = j + 1 basis columns: the product, then the
+// CGS passes of the column class of k.
+template <int KP>
+static void mx_step_kp(MxPlan& P, int c, cudaStream_t s) {
+  gm_gd<float, KP><<<P.g_gd[c], kBlock, 0, s>>>(P.gi);
+  gm_gb<float, KP><<<P.g_gb[c], kBlock, 0, s>>>(P.gi);
+  gm_gc<float, (KP <= 32 ? 32 : 64)><<<P.g_gc[c], kBlock, 0, s>>>(P.gi);
+}
+
+static void mx_step(MxPlan& P, int j, cudaStream_t s) {
+  gm_ga<float><<<P.g_tile, kBlock, 0, s>>>(P.gi);
+  const int c = gm_kclass(j + 1);
+  switch (c) {
+    case 0: mx_step_kp<4>(P, c, s); break;
+    case 1: mx_step_kp<8>(P, c, s); break;
+    case 2: mx_step_kp<16>(P, c, s); break;
+    case 3: mx_step_kp<32>(P, c, s); break;
+    default: mx_step_kp<64>(P, c, s); break;
+  }
+}
+
+// Grids of the FP32 basis kernels (four rows per thread): as many blocks as
+// are resident at each kernel's occupancy.  The FP32 passes are bound by
+// memory, not by the FP64 pipe, so no cap below the occupancy.
+template <int KP>
+static void mx_grids_class(gsk_ctx* ctx, MxPlan& P, int c, int n) {
+  const long long rows4 = ((long long)n + 3) / 4;
+  P.g_gd[c] = ctx->occ_grid((const void*)gm_gd<float, KP>, rows4, kBlock);
+  P.g_gb[c] = ctx->occ_grid((const void*)gm_gb<float, KP>, rows4, kBlock);
+  P.g_gc[c] = ctx->occ_grid((const void*)gm_gc<float, (KP <= 32 ? 32 : 64)>, rows4, kBlock);
 }
 
 static gsk_status mx_record(gsk_ctx* ctx, MxPlan& P, cudaGraphExec_t* exec_out) {
@@ -452,9 +497,10 @@ static gsk_status mx_record(gsk_ctx* ctx, MxPlan& P, cudaGraphExec_t* exec_out) 
   cudaGraphNode_t onode;
   cudaGraph_t obody;
   GSK_CK(add_conditional(top, {}, a.h_outer, cudaGraphCondTypeWhile, 1, &onode, &obody));
-  GSK_CK(cudaGraphConditionalHandleCreate(&a.h_inner, obody, 1u, 0));
-  P.bi.h_while = a.h_inner;
-  P.gi.h_inner = a.h_inner;
+  if (P.solver == 1) {
+    GSK_CK(cudaGraphConditionalHandleCreate(&a.h_inner, obody, 1u, 0));
+    P.bi.h_while = a.h_inner;
+  }
 
   // init: scales W2 (GS(2) of A), the identity test of the metric weights,
   // (W2 A) in FP32, the first FP64 residual
@@ -472,14 +518,21 @@ static gsk_status mx_record(gsk_ctx* ctx, MxPlan& P, cudaGraphExec_t* exec_out) 
 
   Capture cp;
   GSK_CK(cp.begin(cs, obody));
-  if (P.solver == 1) mx_prep_bcg<<<P.g_vec, kBlock, 0, cs>>>(a);
-  else mx_prep_gm<<<P.g_vec, kBlock, 0, cs>>>(a);
-  GSK_CK(cp.end());
-  cudaGraphNode_t inode;
-  cudaGraph_t ibody;
-  GSK_CK(add_conditional(obody, cp.tail, a.h_inner, cudaGraphCondTypeWhile, 1, &inode, &ibody));
-
-  if (P.solver == 1) {
+  if (P.solver == 0) {
+    // GMRES: the cycle start, then the inner cycle's m steps unrolled (no
+    // inner WHILE node; the steps after the cycle has ended return at entry)
+    mx_prep_gm<<<P.g_vec, kBlock, 0, cs>>>(a);
+    for (int j = 0; j < P.m; ++j) mx_step(P, j, cs);
+    mx_gm(P, 4, cs);
+    mx_gm(P, 5, cs);
+    mx_residual<false><<<P.g_tile, kBlock, 0, cs>>>(a);
+    GSK_CK(cp.end());
+  } else {
+    mx_prep_bcg<<<P.g_vec, kBlock, 0, cs>>>(a);
+    GSK_CK(cp.end());
+    cudaGraphNode_t inode;
+    cudaGraph_t ibody;
+    GSK_CK(add_conditional(obody, cp.tail, a.h_inner, cudaGraphCondTypeWhile, 1, &inode, &ibody));
     GSK_CK(cudaGraphConditionalHandleCreate(&P.bi.h_if, ibody, 0u, 0));
     Capture c1;
     GSK_CK(c1.begin(cs, ibody));
@@ -503,17 +556,6 @@ static gsk_status mx_record(gsk_ctx* ctx, MxPlan& P, cudaGraphExec_t* exec_out) 
     GSK_CK(c4.begin(cs, obody, {inode}));
     mx_check_bcg<<<P.g_vec, kBlock, 0, cs>>>(a);
     mx_update_bcg<<<P.g_vec, kBlock, 0, cs>>>(a);
-    mx_residual<false><<<P.g_tile, kBlock, 0, cs>>>(a);
-    GSK_CK(c4.end());
-  } else {
-    Capture c1;
-    GSK_CK(c1.begin(cs, ibody));
-    for (int w : {0, 1, 2, 3}) mx_gm(P, w, cs);
-    GSK_CK(c1.end());
-    Capture c4;
-    GSK_CK(c4.begin(cs, obody, {inode}));
-    mx_gm(P, 4, cs);
-    mx_gm(P, 5, cs);
     mx_residual<false><<<P.g_tile, kBlock, 0, cs>>>(a);
     GSK_CK(c4.end());
   }
