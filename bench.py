@@ -357,9 +357,14 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
             "config": config_dict(s, world), "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "roofline": roofline, "cpu_baseline": cpu,
-            "solves": {"bicgstab": {k: i1[k] for k in ("iters", "conv_name", "relres_true", "ms")},
-                       "gmres30": {k: i2[k] for k in ("iters", "restarts", "conv_name", "relres_true", "ms")},
-                       "all_converged_below_tol": ok},
+            "solves": {"bicgstab": dict({k: i1[k] for k in ("iters", "conv_name", "relres_true", "ms")},
+                                        us_per_iter=round(1e3 * i1["ms"] / max(i1["iters"], 1), 2)),
+                       "gmres30": dict({k: i2[k] for k in ("iters", "restarts", "conv_name", "relres_true", "ms")},
+                                       us_per_step=round(1e3 * i2["ms"] / max(i2["iters"], 1), 2)),
+                       "all_converged_below_tol": ok,
+                       # Bi-CGSTAB's count on this system moves with the rounding
+                       # of any summation order (240-370 seen): compare per iteration
+                       "note": "iteration counts are rounding-sensitive; us_per_iter/us_per_step compare kernels"},
             "kernels": kernels,
             "forms": extra,
         }

@@ -165,7 +165,7 @@ static gsk_status bcg_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, voi
 
 // Clears the counters/flags region and uploads the initial state.
 static gsk_status bcg_upload(gsk_ctx* ctx, BcgPlan& P, cudaStream_t st) {
-  const char* end = (const char*)(P.a.red.counters + (P.a.red.maxgrid + kGroup - 1) / kGroup + 1);
+  const char* end = (const char*)(P.a.red.counters + 1);
   GSK_CK(cudaMemsetAsync(ctx->ws, 0, end - (const char*)ctx->ws, st));
   GSK_CK(cudaMemcpyAsync(P.a.S, &P.host_state, sizeof(BcgState), cudaMemcpyHostToDevice, st));
   return GSK_OK;

@@ -9,9 +9,8 @@
 //  * Reductions are deterministic: the assignment of rows to threads depends
 //    only on (n, grid), and every sum is taken in a fixed order, so repeated
 //    runs give bit-identical scalars.
-//  * Cross-block sums use the "last block finishes" pattern in two levels
-//    (groups of kGroup blocks, then the group totals), so no kernel ever waits
-//    on another block and no spin loop exists.
+//  * Cross-block sums use the "last block finishes" pattern, so no kernel
+//    ever waits on another block and no spin loop exists.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -20,7 +19,6 @@
 namespace gsk {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kGroup = 16;  // blocks per first-level reduction group
 
 // error bits written by kernels into a device status word
 enum : int { kErrIndex = 1, kErrZeroRow = 2, kErrNonFinite = 4, kErrTimeout = 8 };
@@ -28,14 +26,13 @@ enum : int { kErrIndex = 1, kErrZeroRow = 2, kErrNonFinite = 4, kErrTimeout = 8 
 // Scratch for one grid-wide reduction site.
 struct GridRed {
   double* partials;    // [nv_max * maxgrid]
-  double* gpartials;   // [nv_max * ngroups(maxgrid)]
-  unsigned* counters;  // [ngroups(maxgrid) + 1], zero between uses
+  unsigned* counters;  // [1], zero between uses
   int maxgrid;         // launches using this site must have gridDim.x <= maxgrid
 };
 
 // Per-thread accumulation type: FP64 data is accumulated in FP64; FP32 data
 // (the inner solves of the mixed-precision path) in FP32, so that an FP32
-// kernel does no FP64 work per element.  Block and grid sums are FP64.
+// kernel does no FP64 work per element.  Grid sums are FP64.
 template <typename T>
 struct AccOf {
   using type = double;
@@ -125,54 +122,40 @@ __device__ __forceinline__ void block_sum(const double (&v)[NV], double* sm, dou
 // Grid-wide deterministic sum of nv block totals blk[k] (shared memory, valid
 // in every thread).  Returns true in every thread of the one block that
 // finishes last; that block then finds the totals in tot[k] (shared).  The
-// counters are reset so the site can be reused by the next launch.
-// The closing blocks spread the sums over all their warps (one warp per
-// value, lanes over the partials, a fixed shuffle tree), so the serial tail
-// of a launch is a few memory round trips, whatever nv is.
+// counter is reset so the site can be reused by the next launch.
+// One level: each block publishes its totals and counts itself in; the last
+// one sums all G partials of each value (one warp per value, lanes over the
+// partials in a fixed order, a fixed shuffle tree).  The serial tail of a
+// launch is then one fence, one atomic and one round of loads: a two-level
+// scheme (groups of blocks, then the group totals) measured longer, its
+// second atomic and fence sitting on the path that every other SM idles on.
 __device__ __forceinline__ bool grid_sum(const double* blk, int nv, const GridRed& R, double* tot) {
   __shared__ int s_last;
   const int G = gridDim.x, b = blockIdx.x;
-  const int g = b / kGroup;
-  const int ng = (G + kGroup - 1) / kGroup;
-  const int gsize = min(kGroup, G - g * kGroup);
   const int nwarps = blockDim.x >> 5;
   if (threadIdx.x == 0) {
     for (int k = 0; k < nv; ++k) R.partials[k * G + b] = blk[k];
     __threadfence();
-    unsigned t = atomicAdd(&R.counters[g], 1u);
-    s_last = (t == (unsigned)(gsize - 1));
+    const unsigned t = atomicAdd(&R.counters[0], 1u);
+    s_last = (t == (unsigned)(G - 1));
   }
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-  // this block closes group g: the sum of its gsize (<= 32) partials per value
   for (int k = warp_id(); k < nv; k += nwarps) {
-    double v = lane_id() < gsize ? __ldcg(R.partials + k * G + g * kGroup + lane_id()) : 0.0;
-    v = warp_allsum(v);
-    if (lane_id() == 0) {
-      R.gpartials[k * ng + g] = v;
-      __threadfence();
+    const double* p = R.partials + (long long)k * G;
+    double v0 = 0.0, v1 = 0.0;
+    int q = lane_id();
+    for (; q + 32 < G; q += 64) {  // two independent chains, loads in flight together
+      v0 += __ldcg(p + q);
+      v1 += __ldcg(p + q + 32);
     }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    R.counters[g] = 0u;
-    __threadfence();
-    unsigned t = atomicAdd(&R.counters[ng], 1u);
-    s_last = (t == (unsigned)(ng - 1));
-  }
-  __syncthreads();
-  if (!s_last) return false;
-  __threadfence();
-  // the last group closes the grid: lanes over the ng group totals
-  for (int k = warp_id(); k < nv; k += nwarps) {
-    double v = 0.0;
-    for (int q = lane_id(); q < ng; q += 32) v += __ldcg(R.gpartials + k * ng + q);
-    v = warp_allsum(v);
+    if (q < G) v0 += __ldcg(p + q);
+    const double v = warp_allsum(v0 + v1);
     if (lane_id() == 0) tot[k] = v;
   }
   __syncthreads();
-  if (threadIdx.x == 0) R.counters[ng] = 0u;
+  if (threadIdx.x == 0) R.counters[0] = 0u;
   return true;
 }
 

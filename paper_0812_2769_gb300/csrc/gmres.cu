@@ -227,7 +227,7 @@ static gsk_status gm_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, void
 }
 
 static gsk_status gm_upload(gsk_ctx* ctx, GmPlan& P, cudaStream_t st) {
-  const char* end = (const char*)(P.a.red.counters + (P.a.red.maxgrid + kGroup - 1) / kGroup + 1);
+  const char* end = (const char*)(P.a.red.counters + 1);
   GSK_CK(cudaMemsetAsync(ctx->ws, 0, end - (const char*)ctx->ws, st));
   GSK_CK(cudaMemcpyAsync(P.a.S, &P.host_state, sizeof(GmState), cudaMemcpyHostToDevice, st));
   return GSK_OK;

@@ -120,10 +120,8 @@ namespace gsk {
 // Reduction scratch for one site sized for `nv` values and `grid` blocks.
 inline GridRed take_red(Arena& a, int grid, int nv) {
   GridRed r;
-  int ng = (grid + kGroup - 1) / kGroup;
   r.partials = a.take<double>((size_t)nv * grid);
-  r.gpartials = a.take<double>((size_t)nv * ng);
-  r.counters = a.take<unsigned>(ng + 1);
+  r.counters = a.take<unsigned>(1);
   r.maxgrid = grid;
   return r;
 }

@@ -583,7 +583,7 @@ static gsk_status mx_solve(gsk_ctx* ctx, int solver, const gsk_csr* A, const voi
     ge = ctx->add_graph(key, ex);
   }
   GSK_CK(cudaEventRecord(ctx->ev0, st));
-  const char* end = (const char*)(P.a.red.counters + (P.a.red.maxgrid + kGroup - 1) / kGroup + 1);
+  const char* end = (const char*)(P.a.red.counters + 1);
   GSK_CK(cudaMemsetAsync(ctx->ws, 0, end - (const char*)ctx->ws, st));
   GSK_CK(cudaMemcpyAsync(P.a.S, &P.hs, sizeof(MxState), cudaMemcpyHostToDevice, st));
   if (solver == 1) GSK_CK(cudaMemcpyAsync(P.a.Sb, &P.hb, sizeof(BcgState), cudaMemcpyHostToDevice, st));
