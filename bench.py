@@ -185,8 +185,8 @@ def kernel_cost(name, step, n, nnz):
     table = {
         "bcg_init": (spmv_b + 2 * V + 3 * V, 2 * nnz + 4 * n),
         "bcg_k1_spmv_dot": (spmv_b + 3 * V, 2 * nnz + 4 * n),
-        "bcg_k2a_s_update": (3 * V, 4 * n),
-        "bcg_k2b_spmv_dot": (spmv_b + 2 * V, 2 * nnz + 4 * n),
+        "bcg_k2a_s_update": (3 * V, 2 * n),
+        "bcg_k2b_spmv_dot": (spmv_b + 2 * V, 2 * nnz + 6 * n),
         "bcg_k3_xr_update": (7 * V, 10 * n),
         "bcg_k4_p_update": (4 * V, 4 * n),
         "bcg_kt_true_residual": (spmv_b + 3 * V, 2 * nnz + 4 * n),

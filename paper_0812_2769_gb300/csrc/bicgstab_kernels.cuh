@@ -3,8 +3,12 @@
 //
 // One iteration is the kernel chain
 //   k1  v = A p,           sigma = <rh, v>, ||v||         -> alpha or breakdown
-//   k2a s = r - alpha v,   ||W s||                         -> half-step exit?
-//   k2b t = A s,           <t, s>, <t, t>                  -> omega or breakdown
+//   k2a s = r - alpha v
+//   k2b t = A s,           ||W s||, <t, s>, <t, t>         -> half-step exit,
+//                                                             omega or breakdown
+// (the half-step test ||W s|| < tol is taken where s is read anyway, in k2b's
+// epilogue: k2a then needs no cross-block reduction, and the product t = A s
+// of the last iteration is the only work done for nothing)
 //   k3  x += alpha p + omega s, r = s - omega t,
 //                          <rh, r>, ||W r||, ||r||         -> beta, flags
 //   then either k4  p = r + beta (p - omega v)             (keep iterating)
@@ -161,79 +165,67 @@ __global__ void __launch_bounds__(kBlock) bcg_k1(BcgArgs<T> a) {
   }
 }
 
-// s = r - alpha v and ||W s||^2, with the weights' presence (WID: W = I) a
-// compile-time choice: a runtime-uniform branch inside the row loop would be
-// if-converted, and the predicated-off FP64 multiply still costs pipe time.
-template <bool WID, typename T, typename Acc>
-__device__ __forceinline__ Acc bcg_k2a_rows(const BcgArgs<T>& a, Acc alpha) {
-  constexpr int R = Vec16<T>::R;
-  const T* __restrict__ r = a.r;
-  const T* __restrict__ v = a.v;
-  T* __restrict__ s = a.s;
-  Acc acc = Acc(0);
-  BCG_VEC_LOOP(a, R) {
-    if (i0 + R <= a.n && (WID || a.vec_ok)) {
-      const Vec16<T> rv = vload(r + i0), vv = vload(v + i0);
-      Vec16<T> sv;
-#pragma unroll
-      for (int q = 0; q < R; ++q) {
-        sv.v[q] = (T)fma(-alpha, (Acc)vv.v[q], (Acc)rv.v[q]);
-        Acc w1 = (Acc)sv.v[q];
-        if (!WID) w1 *= (Acc)__ldg(a.w + i0 + q);
-        acc = fma(w1, w1, acc);
-      }
-      vstore(s + i0, sv);
-    } else {
-      for (int i = i0; i < min(i0 + R, a.n); ++i) {
-        const T s1 = (T)fma(-alpha, (Acc)v[i], (Acc)r[i]);
-        s[i] = s1;
-        Acc w1 = (Acc)s1;
-        if (!WID) w1 *= (Acc)__ldg(a.w + i);
-        acc = fma(w1, w1, acc);
-      }
-    }
-  }
-  return acc;
-}
-
+// s = r - alpha v.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) bcg_k2a(BcgArgs<T> a) {
   BcgState* S = a.S;
   if (S->stop || S->check) return;
-  __shared__ double sm[1 * kBlock], blk[1], tot[1];
   using Acc = typename AccOf<T>::type;
   const Acc alpha = (Acc)S->alpha;
-  const Acc acc = S->w_identity ? bcg_k2a_rows<true>(a, alpha) : bcg_k2a_rows<false>(a, alpha);
-  const double accd[1] = {(double)acc};
-  block_sum<1, kBlock>(accd, sm, blk);
-  if (grid_sum(blk, 1, a.red, tot) && threadIdx.x == 0) {
-    const double mus = sqrt(tot[0]) / S->mu0;
-    S->mu_s = mus;
-    if (mus < S->tol) S->halfexit = 1;
+  constexpr int R = Vec16<T>::R;
+  const T* __restrict__ r = a.r;
+  const T* __restrict__ v = a.v;
+  T* __restrict__ s = a.s;
+  BCG_VEC_LOOP(a, R) {
+    if (i0 + R <= a.n) {
+      const Vec16<T> rv = vload(r + i0), vv = vload(v + i0);
+      Vec16<T> sv;
+#pragma unroll
+      for (int q = 0; q < R; ++q) sv.v[q] = (T)fma(-alpha, (Acc)vv.v[q], (Acc)rv.v[q]);
+      vstore(s + i0, sv);
+    } else {
+      for (int i = i0; i < a.n; ++i) s[i] = (T)fma(-alpha, (Acc)v[i], (Acc)r[i]);
+    }
   }
+}
+
+// t = A s with <t, s>, <t, t> and ||W s||^2 in the epilogue; the weights'
+// presence (WID: W = I) is a compile-time choice, so no predicated-off FP64
+// multiply runs per row.
+template <bool WID, typename T, typename Acc>
+__device__ __forceinline__ void bcg_k2b_rows(const BcgArgs<T>& a, PipeSmem<T>& pipe, Acc (&acc)[3]) {
+  const T* __restrict__ sv = a.s;
+  T* __restrict__ tout = a.t;
+  spmv_rows_tma(a.rowptr, a.colidx, a.val, a.s_in, a.n, a.nnz, pipe, a.err, [&](int i, T t) {
+    tout[i] = t;
+    const Acc si = (Acc)sv[i];
+    acc[0] = fma((Acc)t, si, acc[0]);
+    acc[1] = fma((Acc)t, (Acc)t, acc[1]);
+    const Acc ws = WID ? si : (Acc)__ldg(a.w + i) * si;
+    acc[2] = fma(ws, ws, acc[2]);
+  });
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) bcg_k2b(BcgArgs<T> a) {
   BcgState* S = a.S;
-  if (S->stop || S->check || S->halfexit) return;
+  if (S->stop || S->check) return;
   __shared__ PipeSmem<T> pipe;
-  __shared__ double blk[2], tot[2];
+  __shared__ double blk[3], tot[3];
   double* sm = reinterpret_cast<double*>(&pipe);  // reduction scratch after the product
   using Acc = typename AccOf<T>::type;
-  const T* __restrict__ sv = a.s;
-  T* __restrict__ tout = a.t;
-  Acc acc[2] = {Acc(0), Acc(0)};
-  spmv_rows_tma(a.rowptr, a.colidx, a.val, a.s_in, a.n, a.nnz, pipe, a.err, [&](int i, T t) {
-    tout[i] = t;
-    acc[0] = fma((Acc)t, (Acc)sv[i], acc[0]);
-    acc[1] = fma((Acc)t, (Acc)t, acc[1]);
-  });
-  const double accd[2] = {(double)acc[0], (double)acc[1]};
-  block_sum<2, kBlock>(accd, sm, blk);
-  if (grid_sum(blk, 2, a.red, tot) && threadIdx.x == 0) {
+  Acc acc[3] = {Acc(0), Acc(0), Acc(0)};
+  if (S->w_identity) bcg_k2b_rows<true>(a, pipe, acc);
+  else bcg_k2b_rows<false>(a, pipe, acc);
+  const double accd[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
+  block_sum<3, kBlock>(accd, sm, blk);
+  if (grid_sum(blk, 3, a.red, tot) && threadIdx.x == 0) {
+    const double mus = sqrt(tot[2]) / S->mu0;
+    S->mu_s = mus;
     if (*(volatile int*)a.err) {
       S->stop = 1;
+    } else if (mus < S->tol) {
+      S->halfexit = 1;  // x += alpha p in k3; this t is not used
     } else if (!(tot[1] > 0.0)) {
       S->conv = GSK_BREAKDOWN;
       S->stop = 1;
@@ -263,7 +255,7 @@ __device__ __forceinline__ void bcg_k3_row(const BcgArgs<T>& a, int i, Acc alpha
 
 // x += alpha p + omega s (p_in, s_in with a preconditioner: PRE),
 // r = s - omega t, and the sums (r^, r), ||W r||^2 and (weights present)
-// ||r||^2; WID as in bcg_k2a_rows.
+// ||r||^2; WID as in bcg_k2b_rows.
 template <bool WID, bool PRE, typename T, typename Acc>
 __device__ __forceinline__ void bcg_k3_rows(const BcgArgs<T>& a, Acc alpha, Acc omega, Acc (&acc)[3]) {
   constexpr int R = Vec16<T>::R;
