@@ -150,8 +150,7 @@ __global__ void __launch_bounds__(kBlock) bcg_k1(BcgArgs<T> a) {
     acc[0] = fma((Acc)rh[i], (Acc)v, acc[0]);
     acc[1] = fma((Acc)v, (Acc)v, acc[1]);
   });
-  const double accd[2] = {(double)acc[0], (double)acc[1]};
-  block_sum<2, kBlock>(accd, sm, blk);
+  block_sum<2, kBlock>(acc, reinterpret_cast<Acc*>(sm), blk);
   if (grid_sum(blk, 2, a.red, tot) && threadIdx.x == 0) {
     const double sigma = tot[0], vn = sqrt(tot[1]);
     if (*(volatile int*)a.err) {
@@ -217,8 +216,7 @@ __global__ void __launch_bounds__(kBlock) bcg_k2b(BcgArgs<T> a) {
   Acc acc[3] = {Acc(0), Acc(0), Acc(0)};
   if (S->w_identity) bcg_k2b_rows<true>(a, pipe, acc);
   else bcg_k2b_rows<false>(a, pipe, acc);
-  const double accd[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
-  block_sum<3, kBlock>(accd, sm, blk);
+  block_sum<3, kBlock>(acc, reinterpret_cast<Acc*>(sm), blk);
   if (grid_sum(blk, 3, a.red, tot) && threadIdx.x == 0) {
     const double mus = sqrt(tot[2]) / S->mu0;
     S->mu_s = mus;
@@ -316,8 +314,7 @@ __global__ void __launch_bounds__(kBlock) bcg_k3(BcgArgs<T> a) {
   Acc acc[3] = {Acc(0), Acc(0), Acc(0)};
   if (wid) bcg_k3_rows<true, PRE>(a, alpha, omega, acc);
   else bcg_k3_rows<false, PRE>(a, alpha, omega, acc);
-  const double accd[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
-  block_sum<3, kBlock>(accd, sm, blk);
+  block_sum<3, kBlock>(acc, reinterpret_cast<Acc*>(sm), blk);
   if (grid_sum(blk, 3, a.red, tot) && threadIdx.x == 0) {
     S->iters += 1;
     const double mur = sqrt(tot[1]) / S->mu0;

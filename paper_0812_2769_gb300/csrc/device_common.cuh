@@ -95,8 +95,11 @@ __device__ __forceinline__ void block_sum_table(TT* tab, int nv, double* res) {
 // active threads) and one warp finishes with shuffles: about 12 warp-wide
 // FP64 additions per value instead of 45 for a shuffle tree in every warp,
 // which matters on a part with little FP64 throughput.
-template <int NV, int BLOCK>
-__device__ __forceinline__ void block_sum(const double (&v)[NV], double* sm, double* res) {
+// The tree runs in the values' type A: FP64 for FP64 data, FP32 for the
+// FP32 inner solves (whose per-thread sums are FP32 already); the totals are
+// returned in FP64 for the grid-wide sum.
+template <int NV, int BLOCK, typename A>
+__device__ __forceinline__ void block_sum(const A (&v)[NV], A* sm, double* res) {
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < NV; ++k) sm[k * BLOCK + threadIdx.x] = v[k];
@@ -112,8 +115,8 @@ __device__ __forceinline__ void block_sum(const double (&v)[NV], double* sm, dou
   if (warp_id() == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      const double t = warp_allsum(sm[k * BLOCK + lane_id()]);
-      if (lane_id() == 0) res[k] = t;
+      const A t = warp_allsum(sm[k * BLOCK + lane_id()]);
+      if (lane_id() == 0) res[k] = (double)t;
     }
   }
   __syncthreads();

@@ -180,9 +180,10 @@ __global__ void __launch_bounds__(kBlock) mx_prep_bcg(MxArgs a) {
   }
 }
 
-// The inner Bi-CGSTAB met its tolerance, broke down or hit its cap: end it.
-__global__ void mx_inner_finish(MxArgs a) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(a.h_inner, 0u);
+// After a round of inner Bi-CGSTAB iterations: go on unless one of them met
+// the inner tolerance, broke down or hit the cap.
+__global__ void mx_inner_next(MxArgs a) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(a.h_inner, (a.Sb->check || a.Sb->stop) ? 0u : 1u);
 }
 
 // Counts non-finite entries of the FP32 correction; a correction that is not
@@ -394,6 +395,7 @@ static gsk_status mx_prepare(gsk_ctx* ctx, int solver, const gsk_csr* A, const v
     bi.cnt = a.cnt;
     bi.err = a.err;
     bi.in_graph = 1;
+    bi.unrolled = 1;
     bi.vec_ok = 1;  // every FP32 vector is workspace (256-byte aligned)
     std::memset(&P.hb, 0, sizeof(P.hb));
     P.hb.tol = opts.inner_tol;
@@ -437,6 +439,8 @@ static gsk_status mx_prepare(gsk_ctx* ctx, int solver, const gsk_csr* A, const v
   }
   return GSK_OK;
 }
+
+constexpr int kMxUnroll = 4;  // inner Bi-CGSTAB iterations per loop-body pass
 
 template <int KP>
 static void mx_launch_gm(MxPlan& P, int which, cudaStream_t s) {
@@ -533,25 +537,20 @@ static gsk_status mx_record(gsk_ctx* ctx, MxPlan& P, cudaGraphExec_t* exec_out) 
     cudaGraphNode_t inode;
     cudaGraph_t ibody;
     GSK_CK(add_conditional(obody, cp.tail, a.h_inner, cudaGraphCondTypeWhile, 1, &inode, &ibody));
-    GSK_CK(cudaGraphConditionalHandleCreate(&P.bi.h_if, ibody, 0u, 0));
+    // inner body: kMxUnroll iterations in a row (kernels after the iteration
+    // that set check or stop return at entry), then the loop condition; no
+    // conditional node per iteration
     Capture c1;
     GSK_CK(c1.begin(cs, ibody));
-    bcg_k1<float><<<P.g_tile, kBlock, 0, cs>>>(P.bi);
-    bcg_k2a<float><<<P.g_vec2, kBlock, 0, cs>>>(P.bi);
-    bcg_k2b<float><<<P.g_tile, kBlock, 0, cs>>>(P.bi);
-    bcg_k3<float><<<P.g_vec2, kBlock, 0, cs>>>(P.bi);
+    for (int u = 0; u < kMxUnroll; ++u) {
+      bcg_k1<float><<<P.g_tile, kBlock, 0, cs>>>(P.bi);
+      bcg_k2a<float><<<P.g_vec2, kBlock, 0, cs>>>(P.bi);
+      bcg_k2b<float><<<P.g_tile, kBlock, 0, cs>>>(P.bi);
+      bcg_k3<float><<<P.g_vec2, kBlock, 0, cs>>>(P.bi);
+      bcg_k4<float><<<P.g_vec2, kBlock, 0, cs>>>(P.bi);
+    }
+    mx_inner_next<<<1, 32, 0, cs>>>(a);
     GSK_CK(c1.end());
-    cudaGraphNode_t ifn;
-    cudaGraph_t ib[2];
-    GSK_CK(add_conditional(ibody, c1.tail, P.bi.h_if, cudaGraphCondTypeIf, 2, &ifn, ib));
-    Capture c2;
-    GSK_CK(c2.begin(cs, ib[0]));
-    mx_inner_finish<<<1, 32, 0, cs>>>(a);
-    GSK_CK(c2.end());
-    Capture c3;
-    GSK_CK(c3.begin(cs, ib[1]));
-    bcg_k4<float><<<P.g_vec2, kBlock, 0, cs>>>(P.bi);
-    GSK_CK(c3.end());
     Capture c4;
     GSK_CK(c4.begin(cs, obody, {inode}));
     mx_check_bcg<<<P.g_vec, kBlock, 0, cs>>>(a);
