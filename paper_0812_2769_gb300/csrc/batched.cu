@@ -334,8 +334,21 @@ __device__ bool block_gs(const BatchSys& S, double* d, double* w2, bool need_w2,
   return true;
 }
 
+// Register budget of the batched Bi-CGSTAB kernel, as the minimum number of
+// resident blocks per SM given to __launch_bounds__ (0: the compiler's own
+// choice).  Measured on the 4096-system batch (2D inclusions, side 16..128):
+// FP64 at 256 threads is fastest with the compiler's choice (496 ms); the
+// mixed kernel at 256 threads is 13% faster held to 3 blocks per SM (80
+// registers; 502 ms against 577 ms at its best before), and both 128-thread
+// instances gain from 6 blocks per SM.  (batch_gmres keeps the compiler's
+// choice: held to 3 or 4 blocks per SM it ran 41% and 73% longer.)
 template <int BS, bool MIXED>
-__global__ void __launch_bounds__(BS) batch_bicgstab(BatchParams P) {
+constexpr int batch_min_blocks() {
+  return BS == 128 ? 6 : (MIXED ? (BS == 256 ? 3 : 1) : 0);
+}
+
+template <int BS, bool MIXED>
+__global__ void __launch_bounds__(BS, (batch_min_blocks<BS, MIXED>())) batch_bicgstab(BatchParams P) {
   __shared__ double sm[3 * BS];
   __shared__ int s_idx, s_err;
   char* slot = P.scratch + (long long)blockIdx.x * P.slot_bytes;
