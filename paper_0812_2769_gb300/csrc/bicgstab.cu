@@ -63,7 +63,6 @@ static gsk_status bcg_record(gsk_ctx* ctx, BcgPlan& P, cudaGraphExec_t* exec_out
   } guard{top};
   BcgArgs<double>& a = P.a;
   a.in_graph = 1;
-  a.unrolled = 1;
   GSK_CK(cudaGraphConditionalHandleCreate(&a.h_while, top, 1u, cudaGraphCondAssignDefault));
 
   Capture c0;
@@ -150,8 +149,7 @@ static gsk_status bcg_prepare(gsk_ctx* ctx, const gsk_csr* A, const void* b, voi
   P.a.p_in = P.pre ? P.ph : P.a.p;
   P.a.s_in = P.pre ? P.sh : P.a.s;
   P.a.in_graph = 0;
-  P.a.unrolled = 0;
-  P.a.h_while = P.a.h_if = 0;
+  P.a.h_while = 0;
   P.a.vec_ok = ((uintptr_t)x % 16 == 0) && (P.a.w == nullptr || (uintptr_t)P.a.w % 16 == 0);
   BcgState& hs = P.host_state;
   std::memset(&hs, 0, sizeof(hs));

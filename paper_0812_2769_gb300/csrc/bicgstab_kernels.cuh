@@ -14,12 +14,13 @@
 //   then either k4  p = r + beta (p - omega v)             (keep iterating)
 //   or          kt  t = b - A x, ||W t||, ||t||            (true residual)
 //               kr  finish, or refresh r = rh = p = t
-// The chain is recorded once into a CUDA graph: a WHILE node repeats the
-// iteration and an IF/ELSE node picks k4 or kt+kr, both driven by values the
-// kernels set on the device, so a solve is one graph launch.  The same
-// kernels can also be driven from a host loop with a CUDA event around each
-// launch (gsk_profile_solve); every kernel then checks the device flags
-// itself, which the graph's conditional nodes make redundant.
+// The chain is recorded once into a CUDA graph: a WHILE node whose body holds
+// several iterations k1..k4 in a row, then kt and kr.  Every kernel checks
+// the device flags at entry: after the iteration that set check or stop the
+// remaining ones return at once, and kt/kr work only when one did; kr sets
+// the WHILE condition.  A solve is one graph launch.  The same kernels can
+// also be driven from a host loop with a CUDA event around each launch
+// (gsk_profile_solve).
 //
 // The breakdown tolerance is 1e-16 * DBL_EPSILON relative to the vector
 // norms (Sec. 2.2).  The stopping metric is ||W(b - Ax)|| / ||W(b - Ax0)||
@@ -58,12 +59,8 @@ struct BcgArgs {
   GridRed red;
   unsigned* cnt;
   int* err;
-  cudaGraphConditionalHandle h_while, h_if;
+  cudaGraphConditionalHandle h_while;
   int in_graph;
-  // unrolled loop body: the graph holds several iterations k1..k4 in a row,
-  // then kt, kr, without an IF node; once an iteration has set check or stop
-  // the following kernels return at entry
-  int unrolled;
   int vec_ok;  // x (and w, if any) are 16-byte aligned: 128-bit loads allowed
 };
 
@@ -290,11 +287,7 @@ __device__ __forceinline__ void bcg_k3_rows(const BcgArgs<T>& a, Acc alpha, Acc 
 template <typename T, bool PRE = false>
 __global__ void __launch_bounds__(kBlock) bcg_k3(BcgArgs<T> a) {
   BcgState* S = a.S;
-  if (a.unrolled && (S->stop || S->check)) return;
-  if (S->stop) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(a, a.h_if, 1u);
-    return;
-  }
+  if (S->stop || S->check) return;
   using Acc = typename AccOf<T>::type;
   const Acc alpha = (Acc)S->alpha;
   if (S->halfexit) {
@@ -304,7 +297,6 @@ __global__ void __launch_bounds__(kBlock) bcg_k3(BcgArgs<T> a) {
       S->iters += 1;
       S->mu_rec = S->mu_s;
       S->check = 1;
-      if (!a.unrolled) set_cond(a, a.h_if, 1u);
     }
     return;
   }
@@ -341,14 +333,13 @@ __global__ void __launch_bounds__(kBlock) bcg_k3(BcgArgs<T> a) {
     }
     S->check = check;
     S->stop = stop;
-    if (!a.unrolled) set_cond(a, a.h_if, (unsigned)(check | stop));
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) bcg_k4(BcgArgs<T> a) {
   const BcgState* S = a.S;
-  if (S->check || S->stop) return;  // the graph's IF node already excludes this
+  if (S->check || S->stop) return;
   using Acc = typename AccOf<T>::type;
   const Acc beta = (Acc)S->beta, omega = (Acc)S->omega;
   const T* __restrict__ r = a.r;

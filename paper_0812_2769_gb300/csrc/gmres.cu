@@ -33,7 +33,7 @@ static void gm_launch_kp(gsk_ctx* ctx, GmPlan& P, int k, cudaStream_t s) {
     case kKUnitCheck: launch_unit_check(ctx, a.n, P.wbuf, a.red, &a.S->w_identity, s); break;
     case kKGmInit: gm_residual<double, true><<<P.g_tile, kBlock, 0, s>>>(a); break;
     case kKGmGa: gm_ga<double><<<P.g_tile, kBlock, 0, s>>>(a); break;
-    case kKGmGy: gm_gy<double><<<1, 32, 0, s>>>(a); break;
+    case kKGmGy: gm_gy<double><<<1, kBlock, 0, s>>>(a); break;
     case kKGmGx: gm_gx<double, KP><<<P.g_gx, kBlock, 0, s>>>(a); break;
     case kKGmGr: gm_residual<double, false><<<P.g_tile, kBlock, 0, s>>>(a); break;
     case kGmIluV: {

@@ -473,13 +473,15 @@ __global__ void gm_gy(GmArgs<T> a) {
   __shared__ double Hs[kMaxM * kMaxM];
   __shared__ double ys[kMaxM], gs[kMaxM];
   const int k = a.S->kcols, ld = a.m + 1, lane = lane_id();
-  if (threadIdx.x >= 32) return;
-  for (int e = lane; e < k * k; e += 32) {
+  // the whole block stages the triangle (its loads in flight together), then
+  // one warp solves
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     const int col = e / k, row = e - col * k;
     if (row <= col) Hs[row * kMaxM + col] = a.H[(long long)col * ld + row];
   }
-  for (int i = lane; i < k; i += 32) gs[i] = a.g[i];
-  __syncwarp();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) gs[i] = a.g[i];
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
   for (int i = k - 1; i >= 0; --i) {
     double s = 0.0;
     for (int q = i + 1 + lane; q < k; q += 32) s = fma(Hs[i * kMaxM + q], ys[q], s);

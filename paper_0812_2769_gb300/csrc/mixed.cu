@@ -395,7 +395,6 @@ static gsk_status mx_prepare(gsk_ctx* ctx, int solver, const gsk_csr* A, const v
     bi.cnt = a.cnt;
     bi.err = a.err;
     bi.in_graph = 1;
-    bi.unrolled = 1;
     bi.vec_ok = 1;  // every FP32 vector is workspace (256-byte aligned)
     std::memset(&P.hb, 0, sizeof(P.hb));
     P.hb.tol = opts.inner_tol;
@@ -445,7 +444,7 @@ constexpr int kMxUnroll = 4;  // inner Bi-CGSTAB iterations per loop-body pass
 template <int KP>
 static void mx_launch_gm(MxPlan& P, int which, cudaStream_t s) {
   switch (which) {
-    case 4: gm_gy<float><<<1, 32, 0, s>>>(P.gi); break;
+    case 4: gm_gy<float><<<1, kBlock, 0, s>>>(P.gi); break;
     case 5: mx_update_gm<KP><<<P.g_vec, kBlock, 0, s>>>(P.a); break;
   }
 }

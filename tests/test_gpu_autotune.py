@@ -3,12 +3,11 @@ shapes on a sample of a C4-style batch, returns one of them, caches it, and
 the caller's data is untouched by the tuning."""
 import time
 
-import numpy as np
 import pytest
 
 import oracle
 from gpu_util import gsk
-from problems import cd, configs
+from problems import configs
 
 pytestmark = pytest.mark.gpu
 

@@ -14,11 +14,6 @@ from problems import cd, configs
 pytestmark = pytest.mark.gpu
 
 
-def _with_diag(rp, ci, va, n):
-    """random_csr rows hold their diagonal and sorted columns already."""
-    return rp, ci, va
-
-
 @pytest.mark.parametrize("case", ["c1", "c2_21", "random"])
 def test_ilu0_apply_matches_oracle(case):
     import torch

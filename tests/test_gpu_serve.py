@@ -3,14 +3,12 @@ scalings arrive while others run; each result equals the same request solved
 alone (bit for bit: a solve's arithmetic does not depend on what runs beside
 it), and every converged result meets the FP64 metric (recomputed by the
 oracle)."""
-import math
 
 import numpy as np
 import pytest
 
 import oracle
 from gpu_util import gsk
-from problems import cd
 from problems import serving as sv
 
 pytestmark = pytest.mark.gpu
