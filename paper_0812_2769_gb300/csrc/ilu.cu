@@ -46,6 +46,58 @@ __global__ void __launch_bounds__(kIluBlock) ilu_factor_kernel(IluArgs a, double
   }
 }
 
+// A row of a sweep with its index data loaded ahead of the level: the row,
+// the range [k0, k1) of its entries in the sweep's triangle, the first
+// kIluPre of those (column, factor entry) and, backward, the pivot.  None of
+// it depends on z, so a thread loads the next level's row while it works on
+// the current one and waits at the barrier; after the barrier only the loads
+// of z remain on the level's critical path (a level's cost was its chain of
+// dependent loads: level pointer, row, columns, z).
+constexpr int kIluPre = 4;
+struct IluRow {
+  int i, k0, k1, cnt;  // cnt: rows in the level
+  int col[kIluPre];
+  double val[kIluPre];
+  double pivot;
+};
+
+__device__ __forceinline__ IluRow ilu_fetch(const IluArgs& a, bool upper, int lev, int tid) {
+  IluRow w;
+  w.i = -1;
+  w.k0 = w.k1 = w.cnt = 0;
+  w.pivot = 1.0;
+  const int* lptr = upper ? a.lptrU : a.lptrL;
+  if (lev >= (upper ? a.nlevU : a.nlevL)) return w;
+  const int l0 = lptr[lev];
+  w.cnt = lptr[lev + 1] - l0;
+  if (tid >= w.cnt) return w;
+  const int i = (upper ? a.orderU : a.orderL)[l0 + tid];
+  const int di = a.dpos[i];
+  w.i = i;
+  w.k0 = upper ? di + 1 : a.rowptr[i];
+  w.k1 = upper ? a.rowptr[i + 1] : di;
+  if (upper) w.pivot = a.lu[di];
+#pragma unroll
+  for (int q = 0; q < kIluPre; ++q) {
+    const int k = w.k0 + q;
+    w.col[q] = k < w.k1 ? a.colidx[k] : 0;
+    w.val[q] = k < w.k1 ? a.lu[k] : 0.0;
+  }
+  return w;
+}
+
+// Forward: y_i = r_i - sum_{k<i} l_ik y_k; backward: z_i = (y_i - sum_{j>i}
+// u_ij z_j) / u_ii; the entries in ascending column order either way.
+__device__ __forceinline__ void ilu_row(const IluArgs& a, bool upper, const IluRow& w, const double* r, double* z) {
+  double s = upper ? __ldcg(z + w.i) : r[w.i];
+  const int np = min(w.k1 - w.k0, kIluPre);
+#pragma unroll
+  for (int q = 0; q < kIluPre; ++q)
+    if (q < np) s = fma(-w.val[q], __ldcg(z + w.col[q]), s);
+  for (int k = w.k0 + kIluPre; k < w.k1; ++k) s = fma(-a.lu[k], __ldcg(z + a.colidx[k]), s);
+  z[w.i] = upper ? s / w.pivot : s;
+}
+
 __global__ void __launch_bounds__(kIluBlock) ilu_solve_kernel(IluArgs a) {
   if (ilu_gate_closed(a.gate)) return;  // the same decision in every block
   const double* r = a.gate.base + (a.gate.col ? (long long)(*a.gate.col) * a.gate.stride : 0ll);
@@ -53,28 +105,25 @@ __global__ void __launch_bounds__(kIluBlock) ilu_solve_kernel(IluArgs a) {
   const int nthreads = gridDim.x * kIluBlock;
   const int tid = blockIdx.x * kIluBlock + threadIdx.x;
   unsigned nb = 0;
-  // forward: y_i = r_i - sum_{k<i} l_ik y_k
+  // levels wider than the grid: the rows after a thread's first one are
+  // fetched when they are processed
+  auto rest = [&](bool upper, int lev, int cnt) {
+    for (int t = tid + nthreads; t < cnt; t += nthreads) ilu_row(a, upper, ilu_fetch(a, upper, lev, t), r, z);
+  };
+  IluRow cur = ilu_fetch(a, false, 0, tid);
   for (int lev = 0; lev < a.nlevL; ++lev) {
-    const int l0 = a.lptrL[lev], cnt = a.lptrL[lev + 1] - l0;
-    for (int t = tid; t < cnt; t += nthreads) {
-      const int i = a.orderL[l0 + t];
-      double s = r[i];
-      for (int k = a.rowptr[i]; k < a.dpos[i]; ++k) s = fma(-a.lu[k], __ldcg(z + a.colidx[k]), s);
-      z[i] = s;
-    }
+    const IluRow nxt = lev + 1 < a.nlevL ? ilu_fetch(a, false, lev + 1, tid) : ilu_fetch(a, true, 0, tid);
+    if (cur.i >= 0) ilu_row(a, false, cur, r, z);
+    rest(false, lev, cur.cnt);
     ilu_barrier(a.bar, nb++, a.err);
+    cur = nxt;
   }
-  // backward: z_i = (y_i - sum_{j>i} u_ij z_j) / u_ii
   for (int lev = 0; lev < a.nlevU; ++lev) {
-    const int l0 = a.lptrU[lev], cnt = a.lptrU[lev + 1] - l0;
-    for (int t = tid; t < cnt; t += nthreads) {
-      const int i = a.orderU[l0 + t];
-      const int di = a.dpos[i];
-      double s = __ldcg(z + i);
-      for (int k = di + 1; k < a.rowptr[i + 1]; ++k) s = fma(-a.lu[k], __ldcg(z + a.colidx[k]), s);
-      z[i] = s / a.lu[di];
-    }
+    const IluRow nxt = ilu_fetch(a, true, lev + 1, tid);
+    if (cur.i >= 0) ilu_row(a, true, cur, r, z);
+    rest(true, lev, cur.cnt);
     if (lev + 1 < a.nlevU) ilu_barrier(a.bar, nb++, a.err);
+    cur = nxt;
   }
 }
 
