@@ -410,6 +410,8 @@ def run_gpu(args):
         extra["serving"] = serving_pass(args)
         extra["spectrum"] = spectrum_pass(g, ctx, A, val0, b, b0, s)
         extra["ilu0"] = ilu_pass(g, ctx, A, val0, b, b0, s)
+        extra["c1_32"] = c1_pass(g)
+        extra["c2_scalings"] = c2_scalings_pass(g, ctx, A, val0, b, b0)
 
     if rank == 0:
         # per-solve times from the serial steps (alone on the GPU, so per
@@ -434,6 +436,13 @@ def run_gpu(args):
             "solve_modes": {"headline": "serial" if args.serial_solves else "concurrent (two streams)",
                             ("concurrent" if args.serial_solves else "serial"): other_line},
             "kernels": kernels,
+            # the CSR product alone on the 256^3 matrix, the configuration
+            # where it is purely bandwidth-bound (from forms.c3_256.spmv)
+            "roofline_spmv": ({"kernel": "spmv_kernel (TMA ring), 256^3, FP64", "bound": "hbm",
+                               "achieved": extra["c3_256"]["spmv"]["f64"]["GBps"], "peak": _peaks().get("hbm_gbs"),
+                               "unit": "GB/s", "frac": extra["c3_256"]["spmv"]["f64"]["frac_of_measured_hbm"],
+                               "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+                              if extra and "c3_256" in extra else None),
             "forms": extra,
         }
         print(json.dumps(line), flush=True)
@@ -570,8 +579,97 @@ def c3_pass(g, steps=2000):
         out[name] = {"ms": ms, "us_per_step": 1e3 * ms / max(1, info["iters"]), "iters": info["iters"],
                      "refinements": info["refinements"], "relres_true": info["relres_true"],
                      "conv_name": info["conv_name"]}
+    # the CSR product alone on this matrix (the clean HBM-bound case): FP64
+    # and FP32 values, algorithmic bytes (w + 4) nnz + 4 (n + 1) + 2 w n
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    spmv = {}
+    for name, A1 in (("f64", A), ("f32", g.Csr(A.rowptr, A.colidx, A.val.float()))):
+        xv = torch.ones(s.n, dtype=A1.val.dtype, device="cuda")
+        yv = torch.empty_like(xv)
+        for _ in range(3):
+            g.gsk_spmv(A1, xv, yv)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            g.gsk_spmv(A1, xv, yv)
+        e1.record()
+        torch.cuda.synchronize()
+        us = 1e3 * e0.elapsed_time(e1) / 10
+        w = A1.val.element_size()
+        byt = (w + 4) * s.nnz + 4 * (s.n + 1) + 2 * w * s.n
+        spmv[name] = {"us": round(us, 1), "algorithmic_MB": round(byt / 1e6, 1), "GBps": round(byt / us / 1e3, 1),
+                      "frac_of_measured_hbm": round(byt / us / 1e3 / hbm, 3)}
+        del xv, yv
+    out["spmv"] = spmv
     del A, val0, b0, b, x
     torch.cuda.empty_cache()
+    return out
+
+
+def _peaks():
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(pk)) if os.path.exists(pk) else {}
+
+
+def c1_pass(g):
+    """The 32^2 configuration: latency-bound (the system fits in L2), so
+    microseconds per solve rather than a bandwidth fraction: GMRES(20) and
+    Bi-CGSTAB, unscaled and after GS(2), to 1e-8."""
+    import torch
+
+    from problems import configs
+
+    s = configs.c1()
+    A = g.Csr.from_host(s.rowptr, s.colidx, s.val)
+    val0 = A.val.clone()
+    b0 = torch.as_tensor(s.b, device="cuda")
+    b = b0.clone()
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    ctx = g.Context(torch.cuda.current_device())
+    out = {"n": s.n, "nnz": s.nnz}
+    for scaled in (False, True):
+        A.val.copy_(val0)
+        b.copy_(b0)
+        if scaled:
+            g.gs_scale(A, b, p=2.0, ctx=ctx)
+        for solver in ("gmres20", "bicgstab"):
+            def solve():
+                x.zero_()
+                if solver == "gmres20":
+                    return g.gmres_solve(A, b, x, m=20, tol=TOL, ctx=ctx)
+                return g.bicgstab_solve(A, b, x, tol=TOL, ctx=ctx)
+            for _ in range(3):
+                info = solve()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(20):
+                info = solve()
+            dt = (time.perf_counter() - t0) / 20
+            out[("gs2_" if scaled else "unscaled_") + solver] = {
+                "us_per_solve": round(1e6 * dt, 1), "solves_per_s": round(1 / dt, 1), "iters": info["iters"],
+                "conv_name": info["conv_name"], "relres_true": info["relres_true"]}
+    return out
+
+
+def c2_scalings_pass(g, ctx, A, val0, b, b0):
+    """The benchmark system under the other scalings the configuration names:
+    unscaled, GS(1) and GS(inf) (GS(2) is the headline); both solvers to 1e-8,
+    at most 10,000 iterations."""
+    import torch
+
+    out = {}
+    for name, p in (("unscaled", None), ("gs1", 1.0), ("gs_inf", math.inf)):
+        row = {}
+        for solver in ("bicgstab", "gmres30"):
+            A.val.copy_(val0)
+            b.copy_(b0)
+            if p is not None:
+                g.gs_scale(A, b, p=p, ctx=ctx)
+            x = torch.zeros_like(b)
+            info = (g.gmres_solve(A, b, x, m=M_GMRES, tol=TOL, ctx=ctx) if solver == "gmres30"
+                    else g.bicgstab_solve(A, b, x, tol=TOL, ctx=ctx))
+            row[solver] = {k: info[k] for k in ("iters", "conv_name", "relres_true", "ms")}
+        out[name] = row
     return out
 
 
@@ -650,23 +748,36 @@ def batched_pass(g, args):
 
 
 def serving_pass(args):
-    """Serving: Poisson arrivals of mixed 2D/3D requests (see problems/serving.py),
-    mixed precision to 1e-8, p50/p99 latency and completed solves per second."""
+    """Serving: mixed 2D/3D requests (see problems/serving.py), mixed
+    precision to 1e-8.  The capacity is measured with every request queued at
+    once; then the same requests arrive as a Poisson stream at 50%, 80% and
+    95% of it, each run reporting p50/p99 latency (arrival to completion) and
+    completed solves per second."""
     from paper_0812_2769_gb300 import serve
     from problems import serving as sv
 
-    rate = 10.0
-    specs = sv.stream(args.serve_requests, rate=rate, seed=7)
-    reqs = [serve.Request(sp.rid, sp.build(), solver=sp.solver, m=sp.m, p=sp.p, tol=TOL, precision="mixed",
-                          arrival=sp.arrival, maxit=3000) for sp in specs]
+    n = args.serve_requests
+    specs = sv.stream(n, rate=1.0, seed=7)
+    systems = [sp.build() for sp in specs]
+
+    def requests(rate):
+        # the stream's request mix does not depend on its rate, only the arrival times
+        arr = [sp.arrival for sp in sv.stream(n, rate=rate, seed=7)] if rate else [0.0] * n
+        return [serve.Request(sp.rid, sysm, solver=sp.solver, m=sp.m, p=sp.p, tol=TOL, precision="mixed",
+                              arrival=t, maxit=3000) for sp, sysm, t in zip(specs, systems, arr)]
+
     be = serve.GpuBackend(0, slots=6)
-    serve.Server(be, slots=6).run(reqs[:3], realtime=False)  # warm the contexts
-    srv = serve.Server(be, slots=6)
-    res = srv.run(reqs, realtime=True)
-    out = serve.summarize(res)
-    out.update({"arrival_rate_per_s": rate, "slots": 6, "peak_admitted_GB": round(srv.peak_in_use / 1e9, 3),
-                "maxit": 3000})
-    return out
+    serve.Server(be, slots=6).run(requests(None)[:3], realtime=False)  # warm the contexts
+    sat = serve.summarize(serve.Server(be, slots=6).run(requests(None), realtime=False))
+    capacity = sat["solves_per_s"]
+    loads = {}
+    for f in (0.5, 0.8, 0.95):
+        srv = serve.Server(be, slots=6)
+        out = serve.summarize(srv.run(requests(f * capacity), realtime=True))
+        out.update({"arrival_rate_per_s": round(f * capacity, 3), "peak_admitted_GB": round(srv.peak_in_use / 1e9, 3)})
+        loads[f"{round(100 * f)}%"] = out
+    return {"requests_per_run": n, "slots": 6, "maxit": 3000, "capacity_solves_per_s": capacity,
+            "capacity_run": {k: sat[k] for k in ("completed", "converged", "p50_s", "p99_s")}, "loads": loads}
 
 
 def profile_pass(g, ctx, A, val0, b, b0, s):
