@@ -11,7 +11,8 @@ are independent (both read the scaled A and b): they run concurrently on two
 CUDA streams, each with its own library context, so that one solver's kernels
 fill the SMs the other's leave idle at kernel boundaries.  The same steps
 with the solves one after the other are timed as well ("serial" in the
-line; --serial-solves makes that the headline).
+line); --serial-solves runs only that form (the one to use under a
+profiler, which serialises the two host threads' launches).
 
 Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) execute one
 independent replica per GPU (weak scaling, no data-path collective); the
@@ -63,7 +64,8 @@ def parse_args(argv=None):
     ap.add_argument("--gmres-iters", type=int, default=30, help="Arnoldi steps in --profile-kernels")
     ap.add_argument("--bicgstab-iters", type=int, default=20, help="Bi-CGSTAB iterations in --profile-kernels")
     ap.add_argument("--serial-solves", action="store_true",
-                    help="run a step's two solves one after the other (default: concurrently on two streams)")
+                    help="run a step's two solves one after the other, and no concurrent step at all "
+                         "(default: concurrently on two streams, the serial form timed beside it)")
     return ap.parse_args(argv)
 
 
@@ -327,23 +329,26 @@ def run_gpu(args):
     solves_done = sum_over_ranks(dist, SOLVES_PER_STEP * args.steps)
     value = solves_done / t_max
 
-    # the other mode (serial when the headline ran concurrently, and back),
-    # same steps, same timing; its per-solve times are the solvers' own
-    other = not args.serial_solves
-    for _ in range(2):
-        step(other)
-    torch.cuda.synchronize()
-    barrier(dist, local)
-    e2 = torch.cuda.Event(enable_timing=True)
-    e3 = torch.cuda.Event(enable_timing=True)
-    e2.record(stream)
-    infos_other = [step(other) for _ in range(args.steps)]
-    e3.record(stream)
-    torch.cuda.synchronize()
-    t_other = max_over_ranks(dist, e2.elapsed_time(e3) / 1e3)
-    other_line = {"value": sum_over_ranks(dist, SOLVES_PER_STEP * args.steps) / t_other, "unit": UNIT,
-                  "ms_per_step": t_other * 1e3 / args.steps}
-    serial_infos = infos_other if other else infos
+    # with the concurrent headline, the same steps with the solves one after
+    # the other, same timing; their per-solve times are the solvers' own.
+    # (--serial-solves runs no concurrent step at all: the form to use under
+    # a profiler, which serialises the two host threads' launches.)
+    other_line = None
+    serial_infos = infos
+    if not args.serial_solves:
+        for _ in range(2):
+            step(True)
+        torch.cuda.synchronize()
+        barrier(dist, local)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        serial_infos = [step(True) for _ in range(args.steps)]
+        e3.record(stream)
+        torch.cuda.synchronize()
+        t_other = max_over_ranks(dist, e2.elapsed_time(e3) / 1e3)
+        other_line = {"value": sum_over_ranks(dist, SOLVES_PER_STEP * args.steps) / t_other, "unit": UNIT,
+                      "ms_per_step": t_other * 1e3 / args.steps}
 
     # kernels launched in the timed region (per step: 2 for GS(2); each solve
     # from its counters -- see the launch structure of the two graphs)
@@ -433,8 +438,8 @@ def run_gpu(args):
                        # of any summation order (240-370 seen): compare per iteration
                        "note": "iteration counts are rounding-sensitive; us_per_iter/us_per_step compare kernels",
                        "timing": "ms, us_per_iter, us_per_step from the serial steps (each solve alone)"},
-            "solve_modes": {"headline": "serial" if args.serial_solves else "concurrent (two streams)",
-                            ("concurrent" if args.serial_solves else "serial"): other_line},
+            "solve_modes": ({"headline": "serial"} if args.serial_solves else
+                            {"headline": "concurrent (two streams)", "serial": other_line}),
             "kernels": kernels,
             # the CSR product alone on the 256^3 matrix, the configuration
             # where it is purely bandwidth-bound (from forms.c3_256.spmv)
@@ -446,6 +451,7 @@ def run_gpu(args):
             "forms": extra,
         }
         print(json.dumps(line), flush=True)
+    pool.shutdown(wait=True)
     if dist is not None:
         dist.destroy_process_group()
 
