@@ -208,6 +208,7 @@ def kernel_cost(name, step, n, nnz):
         "gm_gb_cgs_pass2": ((k + 2) * V, 4 * k * n),
         "gm_gc_cgs_pass3_givens": ((k + 2) * V, 2 * k * n + 2 * n),
         "gm_gx_x_update": ((k + 2) * V, 2 * k * n),
+        "gm_gy_backsolve": (8 * (k * (k + 1) // 2 + 2 * k), k * k),
         "gs_norm(w)": (8 * nnz + 4 * (n + 1) + V, 2 * nnz),
         "unit_check": (V, 0),
     }
