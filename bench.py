@@ -549,6 +549,7 @@ def mixed_pass(g, ctx, A, val0, b, b0, x1, x2, args):
     t = e0.elapsed_time(e1) / 1e3
     i1, i2 = infos[-1]
     return {"value": SOLVES_PER_STEP * K / t, "unit": UNIT, "ms_per_step": 1e3 * t / K, "dtype": "f32 inner, f64 refinement",
+            "solves": "one after the other (compare with solve_modes.serial of the FP64 headline)",
             "bicgstab": {k: i1[k] for k in ("iters", "refinements", "conv_name", "relres_true", "ms")},
             "gmres30": {k: i2[k] for k in ("iters", "refinements", "conv_name", "relres_true", "ms")},
             "all_converged_below_tol": all(a["conv"] == 0 and a["relres_true"] < TOL and c["conv"] == 0
