@@ -61,3 +61,32 @@ def test_binding_refuses_to_run_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(g, "LIB_PATH", str(tmp_path / "libgsk.so"))
     with pytest.raises(ImportError, match="no CPU fallback"):
         g.lib()
+
+
+def test_plain_c_program_builds_and_links_against_the_library(gsk_lib, tmp_path):
+    """The boundary is a C ABI: a C99 program includes include/gsk.h, links
+    libgsk.so and calls its host-only entry points (no GPU involved)."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <string.h>\n#include "gsk.h"\n'
+        "int main(void) {\n"
+        "  gsk_opts o;\n  size_t bytes = 0;\n"
+        "  gsk_opts_default(&o);\n"
+        "  if (o.maxit != 10000 || o.refresh != 3) return 1;\n"
+        "  if (gsk_workspace_bytes(1000, 5000, 1, 0, 0, &bytes) != GSK_OK || bytes == 0) return 2;\n"
+        "  if (gsk_workspace_bytes(10, 10, 0, 0, 0, &bytes) != GSK_ERR_ARG) return 3;\n"
+        "  if (strstr(gsk_version(), \"sm_103a\") == NULL) return 4;\n"
+        "  printf(\"%s\\n\", gsk_version());\n  return 0;\n}\n")
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(gsk_lib.LIB_PATH)
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    "-L", libdir, "-lgsk", "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    assert "sm_103a" in out.stdout
