@@ -192,3 +192,43 @@ def test_full_c2_bicgstab_gs2_properties():
     mu = oracle.relres(s.rowptr, s.colidx, val_s, b_s, xg)
     assert mu < 1e-8 and abs(mu - info["relres_true"]) < 1e-6 * mu
     assert np.linalg.norm(xg - s.x_true) / np.linalg.norm(s.x_true) < 1e-3
+
+
+@pytest.mark.parametrize("seed", [3, 11])
+def test_counts_match_the_oracle_exactly_where_rounding_does_not_matter(seed):
+    """On well-conditioned nonsymmetric systems (the ones on which the oracle
+    matches SciPy step for step) the GPU takes exactly the oracle's number of
+    GMRES(m) steps and Bi-CGSTAB iterations, and reaches the same solution
+    to about the rounding of the summation order."""
+    import torch
+
+    g = gsk()
+    rs = np.random.default_rng(seed)
+    n = 5000
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        c = np.unique(np.concatenate([[i], rs.integers(0, n, 8)]))
+        v = rs.uniform(-1, 1, len(c))
+        v[c == i] = rs.uniform(2, 3) * 9
+        rows.append(len(c))
+        cols.append(c)
+        vals.append(v)
+    rp = np.concatenate([[0], np.cumsum(rows)]).astype(np.int32)
+    ci = np.concatenate(cols).astype(np.int32)
+    va = np.concatenate(vals)
+    b = rs.normal(size=n)
+    s = cd.System(n, rp, ci, va, b)
+    A, bd = to_dev(g, s)
+    o = g.opts(metric=g.METRIC_PLAIN, refresh=0)
+    for tol in (1e-6, 1e-12):
+        for m in (5, 20):
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            info = g.gmres_solve(A, bd, x, m=m, tol=tol, options=o)
+            xo, io = oracle.gmres(rp, ci, va, b, m=m, tol=tol, w=np.ones(n))
+            assert info["conv"] == io["conv"] == 0 and info["iters"] == io["iters"], (m, tol, info, io)
+            assert np.abs(x.cpu().numpy() - xo).max() <= 1e-11 * np.abs(xo).max()
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        info = g.bicgstab_solve(A, bd, x, tol=tol, options=o)
+        xo, io = oracle.bicgstab(rp, ci, va, b, tol=tol, refresh=0, w=np.ones(n))
+        assert info["conv"] == io["conv"] == 0 and info["iters"] == io["iters"], (tol, info, io)
+        assert np.abs(x.cpu().numpy() - xo).max() <= 1e-11 * np.abs(xo).max()
