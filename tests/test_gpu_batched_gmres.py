@@ -150,3 +150,41 @@ def test_batched_gmres_rejects_bad_shapes():
         assert e.value.status == g.ERR_ARG
     with pytest.raises(g.GskError):
         g.gmres_solve_batched(As, bs, xs, m=65, p=2.0, tol=1e-8)
+
+
+def _well_conditioned(seed, n):
+    rs = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        c = np.unique(np.concatenate([[i], rs.integers(0, n, 6)]))
+        v = rs.uniform(-1, 1, len(c))
+        v[c == i] = rs.uniform(2, 3) * 7
+        rows.append(len(c))
+        cols.append(c)
+        vals.append(v)
+    rp = np.concatenate([[0], np.cumsum(rows)]).astype(np.int32)
+    return cd.System(n, rp, np.concatenate(cols).astype(np.int32), np.concatenate(vals), rs.normal(size=n))
+
+
+@pytest.mark.parametrize("solver", ["bicgstab", "gmres"])
+def test_batched_counts_match_the_oracle_exactly_where_rounding_does_not_matter(solver):
+    """Well-conditioned nonsymmetric systems of several sizes, no scaling:
+    each system takes exactly the oracle's iterations (block-level sums in
+    another order do not move the count there) and reaches its solution."""
+    g = gsk()
+    systems = [_well_conditioned(s, n) for s, n in ((1, 300), (2, 1500), (3, 4000), (4, 777))]
+    As, bs, xs = _upload(g, systems)
+    o = g.opts(metric=g.METRIC_PLAIN, refresh=0)
+    nan = float("nan")
+    if solver == "gmres":
+        infos, stat = g.gmres_solve_batched(As, bs, xs, m=10, p=[nan] * 4, tol=1e-10, options=o)
+    else:
+        infos, stat = g.bicgstab_solve_batched(As, bs, xs, p=[nan] * 4, tol=1e-10, options=o)
+    assert all(st == g.OK for st in stat)
+    for s, x, info in zip(systems, xs, infos):
+        if solver == "gmres":
+            xo, io = oracle.gmres(s.rowptr, s.colidx, s.val, s.b, m=10, tol=1e-10, w=np.ones(s.n))
+        else:
+            xo, io = oracle.bicgstab(s.rowptr, s.colidx, s.val, s.b, tol=1e-10, refresh=0, w=np.ones(s.n))
+        assert info["conv"] == io["conv"] == 0 and info["iters"] == io["iters"], (s.n, info, io)
+        assert np.abs(x.cpu().numpy() - xo).max() <= 1e-9 * np.abs(xo).max()
