@@ -240,6 +240,15 @@ gsk_status gsk_ilu0_destroy(gsk_ilu0* ilu);
 gsk_status gsk_ilu0_apply(gsk_ctx* ctx, const gsk_ilu0* ilu, const double* r, double* z, void* stream);
 
 /*
+ * gsk_ilu0_info -- the handle's level schedule: the number of levels of the
+ * forward (L) and backward (U) sweeps, and whether the sweeps run in one
+ * thread block with z in shared memory (1: systems whose z fits there) or
+ * across the grid with a barrier between levels (0).  Host pointers; any
+ * may be NULL.  GSK_ERR_ARG for a NULL handle.
+ */
+gsk_status gsk_ilu0_info(const gsk_ilu0* ilu, int* levels_lower, int* levels_upper, int* one_block);
+
+/*
  * gsk_spmv -- y = A x, the product every Krylov step performs (Sec. 2).
  *   x, y   device [n] of A's dtype; x and y must not overlap.
  * Asynchronous on `stream`.

@@ -85,6 +85,7 @@ SIGNATURES = {
     "gsk_ilu0_create": ([C.c_void_p, C.POINTER(CsrC), C.POINTER(C.c_void_p), C.c_void_p], C.c_int),
     "gsk_ilu0_destroy": ([C.c_void_p], C.c_int),
     "gsk_ilu0_apply": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "gsk_ilu0_info": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gsk_spmv": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "gmres_solve": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                      C.POINTER(OptsC), C.POINTER(InfoC), C.c_void_p], C.c_int),
@@ -258,6 +259,13 @@ class Ilu0:
             z = _torch().empty_like(r)
         self.ctx.check(lib().gsk_ilu0_apply(self.ctx.handle, self._h, _ptr(r), _ptr(z), _stream_ptr(stream)))
         return z
+
+    def info(self) -> dict:
+        """Levels of the forward and backward sweeps and whether they run in
+        one thread block (z in shared memory) or across the grid."""
+        lo, up, one = C.c_int(0), C.c_int(0), C.c_int(0)
+        self.ctx.check(lib().gsk_ilu0_info(self._h, C.byref(lo), C.byref(up), C.byref(one)))
+        return {"levels_lower": lo.value, "levels_upper": up.value, "one_block": bool(one.value)}
 
     def close(self):
         if self._h:

@@ -127,6 +127,78 @@ __global__ void __launch_bounds__(kIluBlock) ilu_solve_kernel(IluArgs a) {
   }
 }
 
+// A level-ordered row of the one-CTA sweep, loaded ahead (every address
+// follows from its position p alone).
+struct IluPRow {
+  int i, k0, k1;
+  int col[kIluPack];
+  double val[kIluPack];
+  double piv;
+};
+
+__device__ __forceinline__ IluPRow ilu_pfetch(const IluPackedSweep& P, int p, bool upper) {
+  IluPRow w;
+  w.i = P.row[p];
+  w.k0 = P.k0[p];
+  w.k1 = P.k1[p];
+#pragma unroll
+  for (int q = 0; q < kIluPack; ++q) {
+    w.col[q] = P.col[kIluPack * p + q];
+    w.val[q] = P.val[kIluPack * p + q];
+  }
+  w.piv = upper ? P.piv[p] : 1.0;
+  return w;
+}
+
+// The row of ilu_row with z in shared memory: the same FMAs in the same order.
+__device__ __forceinline__ void ilu_prow(const IluArgs& a, bool upper, const IluPRow& w, double* zs) {
+  double s = zs[w.i];
+  const int np = min(w.k1 - w.k0, kIluPack);
+#pragma unroll
+  for (int q = 0; q < kIluPack; ++q)
+    if (q < np) s = fma(-w.val[q], zs[w.col[q]], s);
+  for (int k = w.k0 + kIluPack; k < w.k1; ++k) s = fma(-a.lu[k], zs[a.colidx[k]], s);
+  zs[w.i] = upper ? s / w.piv : s;
+}
+
+__global__ void __launch_bounds__(kIluSBlock) ilu_solve_smem(IluArgs a, IluPackedSweep L, IluPackedSweep U) {
+  if (ilu_gate_closed(a.gate)) return;
+  extern __shared__ double zs[];  // [n] z, then the level pointers of both sweeps
+  int* lp = reinterpret_cast<int*>(zs + a.n);
+  const double* r = a.gate.base + (a.gate.col ? (long long)(*a.gate.col) * a.gate.stride : 0ll);
+  const int t = threadIdx.x;
+  for (int i = t; i < a.n; i += kIluSBlock) zs[i] = r[i];
+  for (int q = t; q <= a.nlevL; q += kIluSBlock) lp[q] = a.lptrL[q];
+  for (int q = t; q <= a.nlevU; q += kIluSBlock) lp[a.nlevL + 1 + q] = a.lptrU[q];
+  __syncthreads();
+  for (int sw = 0; sw < 2; ++sw) {
+    const bool upper = sw == 1;
+    const IluPackedSweep& P = upper ? U : L;
+    const int* lev = upper ? lp + a.nlevL + 1 : lp;
+    const int nlev = upper ? a.nlevU : a.nlevL;
+    bool have = lev[0] + t < lev[1];
+    IluPRow cur = have ? ilu_pfetch(P, lev[0] + t, upper) : IluPRow{};
+    for (int l = 0; l < nlev; ++l) {
+      const bool have_next = l + 1 < nlev && lev[l + 1] + t < lev[l + 2];
+      const IluPRow nxt = have_next ? ilu_pfetch(P, lev[l + 1] + t, upper) : IluPRow{};
+      if (have) ilu_prow(a, upper, cur, zs);
+      for (int p = lev[l] + t + kIluSBlock; p < lev[l + 1]; p += kIluSBlock)
+        ilu_prow(a, upper, ilu_pfetch(P, p, upper), zs);
+      __syncthreads();
+      cur = nxt;
+      have = have_next;
+    }
+  }
+  for (int i = t; i < a.n; i += kIluSBlock) a.z[i] = zs[i];
+}
+
+// dst[t] = lu[src[t]] (0 where src[t] < 0): the packed factor entries, taken
+// once after the factorisation.
+__global__ void ilu_gather_kernel(int count, const int* src, const double* lu, double* dst) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x)
+    dst[t] = src[t] >= 0 ? lu[src[t]] : 0.0;
+}
+
 IluArgs ilu_args(const gsk_ilu0* h, const IluGate& gate, double* z) {
   IluArgs a;
   a.n = h->n;
@@ -151,6 +223,13 @@ IluArgs ilu_args(const gsk_ilu0* h, const IluGate& gate, double* z) {
 // cooperative sweep kernel.
 gsk_status ilu_launch_apply(gsk_ctx* ctx, const gsk_ilu0* h, const IluGate& gate, double* z, cudaStream_t st) {
   IluArgs a = ilu_args(h, gate, z);
+  if (h->smem_bytes > 0) {
+    const IluPackedSweep L = {h->prowL, h->pk0L, h->pk1L, h->pcolL, h->pvalL, nullptr};
+    const IluPackedSweep U = {h->prowU, h->pk0U, h->pk1U, h->pcolU, h->pvalU, h->ppiv};
+    ilu_solve_smem<<<1, kIluSBlock, h->smem_bytes, st>>>(a, L, U);
+    GSK_CK(cudaGetLastError());
+    return GSK_OK;
+  }
   GSK_CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
   void* params[] = {&a};
   GSK_CK(cudaLaunchCooperativeKernel((const void*)ilu_solve_kernel, dim3(h->grid), dim3(kIluBlock), params, 0, st));
@@ -162,6 +241,120 @@ gsk_status ilu_read_err(gsk_ctx* ctx, const gsk_ilu0* h, cudaStream_t st) {
   GSK_CK(cudaMemcpyAsync(hb, h->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   GSK_CK(cudaStreamSynchronize(st));
   return err_bits_status(ctx, *hb);
+}
+
+// The one-CTA sweep's data, when z and the level pointers of both sweeps fit
+// in one CTA's shared memory (GSK_ILU_SWEEP=grid keeps the grid sweep): the
+// rows in level order, their triangle's entry range, the first kIluPack
+// columns and (gathered from the factors just computed) entries, the pivots.
+// Any failure here leaves the handle on the grid sweep.
+static void ilu_pack_small(gsk_ctx* ctx, gsk_ilu0* h, const std::vector<int>& rp, const std::vector<int>& ci,
+                           const std::vector<int>& dpos, const std::vector<int>& orderL,
+                           const std::vector<int>& orderU, cudaStream_t st) {
+  const int n = h->n;
+  const char* sweep = std::getenv("GSK_ILU_SWEEP");
+  if (sweep && std::strcmp(sweep, "grid") == 0) return;
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const size_t sbytes = sizeof(double) * (size_t)n + sizeof(int) * (size_t)(h->nlevL + 1 + h->nlevU + 1);
+  if (sbytes + 1024 > (size_t)optin) return;
+  std::vector<int> row[2], k0[2], k1[2], col[2], src[2], psrc(n);
+  for (int sw = 0; sw < 2; ++sw) {
+    const std::vector<int>& order = sw ? orderU : orderL;
+    row[sw].resize(n);
+    k0[sw].resize(n);
+    k1[sw].resize(n);
+    col[sw].assign((size_t)kIluPack * n, 0);
+    src[sw].assign((size_t)kIluPack * n, -1);
+    for (int p = 0; p < n; ++p) {
+      const int i = order[p];
+      const int a0 = sw ? dpos[i] + 1 : rp[i], a1 = sw ? rp[i + 1] : dpos[i];
+      row[sw][p] = i;
+      k0[sw][p] = a0;
+      k1[sw][p] = a1;
+      for (int q = 0; q < kIluPack && a0 + q < a1; ++q) {
+        col[sw][(size_t)kIluPack * p + q] = ci[a0 + q];
+        src[sw][(size_t)kIluPack * p + q] = a0 + q;
+      }
+      if (sw) psrc[p] = dpos[i];
+    }
+  }
+  Arena sz;
+  for (int sw = 0; sw < 2; ++sw) {
+    sz.take<int>(n);
+    sz.take<int>(n);
+    sz.take<int>(n);
+    sz.take<int>((size_t)kIluPack * n);
+    sz.take<int>((size_t)kIluPack * n);
+    sz.take<double>((size_t)kIluPack * n);
+  }
+  sz.take<int>(n);
+  sz.take<double>(n);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, sz.off) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  Arena ar{(char*)mem, sz.off, 0};
+  int *prow[2], *pk0[2], *pk1[2], *pcol[2], *psr[2];
+  double* pval[2];
+  for (int sw = 0; sw < 2; ++sw) {
+    prow[sw] = ar.take<int>(n);
+    pk0[sw] = ar.take<int>(n);
+    pk1[sw] = ar.take<int>(n);
+    pcol[sw] = ar.take<int>((size_t)kIluPack * n);
+    psr[sw] = ar.take<int>((size_t)kIluPack * n);
+    pval[sw] = ar.take<double>((size_t)kIluPack * n);
+  }
+  int* ppsrc = ar.take<int>(n);
+  double* ppiv = ar.take<double>(n);
+  cudaError_t e = cudaSuccess;
+  auto up = [&](void* dst, const void* s, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, s, bytes, cudaMemcpyHostToDevice, st);
+  };
+  for (int sw = 0; sw < 2; ++sw) {
+    up(prow[sw], row[sw].data(), sizeof(int) * n);
+    up(pk0[sw], k0[sw].data(), sizeof(int) * n);
+    up(pk1[sw], k1[sw].data(), sizeof(int) * n);
+    up(pcol[sw], col[sw].data(), sizeof(int) * kIluPack * (size_t)n);
+    up(psr[sw], src[sw].data(), sizeof(int) * kIluPack * (size_t)n);
+  }
+  up(ppsrc, psrc.data(), sizeof(int) * n);
+  const int gg = ctx->grid_for((long long)kIluPack * n, 256, 8);
+  if (e == cudaSuccess) {
+    for (int sw = 0; sw < 2; ++sw) ilu_gather_kernel<<<gg, 256, 0, st>>>(kIluPack * n, psr[sw], h->lu, pval[sw]);
+    ilu_gather_kernel<<<gg, 256, 0, st>>>(n, ppsrc, h->lu, ppiv);
+    e = cudaGetLastError();
+  }
+  // the attribute belongs to the kernel, not the handle: allow the device's
+  // maximum once, so that every handle's launch fits whatever its size
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)ilu_solve_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(mem);
+    return;
+  }
+  h->pmem = mem;
+  h->prowL = prow[0];
+  h->pk0L = pk0[0];
+  h->pk1L = pk1[0];
+  h->pcolL = pcol[0];
+  h->psrcL = psr[0];
+  h->pvalL = pval[0];
+  h->prowU = prow[1];
+  h->pk0U = pk0[1];
+  h->pk1U = pk1[1];
+  h->pcolU = pcol[1];
+  h->psrcU = psr[1];
+  h->pvalU = pval[1];
+  h->ppsrc = ppsrc;
+  h->ppiv = ppiv;
+  h->smem_bytes = (int)sbytes;
 }
 
 }  // namespace gsk
@@ -291,7 +484,16 @@ extern "C" gsk_status gsk_ilu0_create(gsk_ctx* ctx, const gsk_csr* A, gsk_ilu0**
     delete h;
     return rs;
   }
+  ilu_pack_small(ctx, h, rp, ci, dpos, orderL, orderU, st);
   *out = h;
+  return GSK_OK;
+}
+
+extern "C" gsk_status gsk_ilu0_info(const gsk_ilu0* h, int* levels_lower, int* levels_upper, int* one_block) {
+  if (!h) return GSK_ERR_ARG;
+  if (levels_lower) *levels_lower = h->nlevL;
+  if (levels_upper) *levels_upper = h->nlevU;
+  if (one_block) *one_block = h->smem_bytes > 0 ? 1 : 0;
   return GSK_OK;
 }
 
@@ -299,6 +501,7 @@ extern "C" gsk_status gsk_ilu0_destroy(gsk_ilu0* h) {
   if (!h) return GSK_OK;
   cudaSetDevice(h->device);
   cudaFree(h->mem);
+  if (h->pmem) cudaFree(h->pmem);
   delete h;
   return GSK_OK;
 }

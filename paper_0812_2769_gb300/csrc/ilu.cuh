@@ -37,6 +37,14 @@ struct gsk_ilu0 {
   int* err = nullptr;      // error bits of the factorisation and applications
   int nlevL = 0, nlevU = 0;
   int grid = 0;            // blocks of the cooperative launches (all resident)
+  // one-CTA sweep for systems whose z fits in shared memory: the rows of each
+  // sweep in level order with their first kIluPack entries packed, in a
+  // second allocation; smem_bytes = 0 means the cooperative grid sweep
+  void* pmem = nullptr;
+  int smem_bytes = 0;
+  int *prowL = nullptr, *pk0L = nullptr, *pk1L = nullptr, *pcolL = nullptr, *psrcL = nullptr;
+  int *prowU = nullptr, *pk0U = nullptr, *pk1U = nullptr, *pcolU = nullptr, *psrcU = nullptr, *ppsrc = nullptr;
+  double *pvalL = nullptr, *pvalU = nullptr, *ppiv = nullptr;
 };
 
 namespace gsk {
@@ -107,6 +115,24 @@ __device__ __forceinline__ void ilu_barrier(unsigned* bar, unsigned k, int* err)
 
 // z = U^-1 L^-1 r, level by level.
 __global__ void __launch_bounds__(kIluBlock) ilu_solve_kernel(IluArgs a);
+
+// The same sweeps by one CTA with z in shared memory, for systems small
+// enough: a level then ends at __syncthreads instead of a grid barrier, and
+// the rows of the next level (level-ordered, their first kIluPack columns
+// and factor entries packed) are loaded while the current one is summed.
+// The arithmetic of every row is the grid sweep's, in the same order, so the
+// results are bit-identical.
+constexpr int kIluPack = 4;
+constexpr int kIluSBlock = 1024;
+struct IluPackedSweep {
+  const int* row;     // [n] row of level-ordered position p
+  const int* k0;      // [n] first entry of the row's triangle (index into lu / colidx)
+  const int* k1;      // [n] one past its last
+  const int* col;     // [kIluPack n] the first kIluPack columns (0 where the row has fewer)
+  const double* val;  // [kIluPack n] their factor entries (0 where the row has fewer)
+  const double* piv;  // [n] u_ii (backward sweep only; null forward)
+};
+__global__ void __launch_bounds__(kIluSBlock) ilu_solve_smem(IluArgs a, IluPackedSweep L, IluPackedSweep U);
 
 // One application recorded on `st` (capturable into a graph): the barrier
 // counter is cleared, then the cooperative sweep runs (or returns at once if

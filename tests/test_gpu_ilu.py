@@ -129,3 +129,44 @@ def test_gpu_ilu_matches_printed_table(row, tol):
                                                   m=row["m"] or 10, precond=True)
     assert pt.matches(row["solver"], row["entries"][tol], conv, iters, relres), (row["entries"][tol], conv, iters,
                                                                                  relres)
+
+
+@pytest.mark.parametrize("case", ["c1", "c2_21", "random", "p1_128"])
+def test_one_block_sweep_is_bit_identical_to_the_grid_sweep(case, monkeypatch):
+    """Systems whose z fits in shared memory are swept by one thread block
+    (a level ends at a block barrier): the same per-row arithmetic in the
+    same order as the grid sweep, so the results are bit-identical."""
+    import torch
+
+    g = gsk()
+    if case == "c1":
+        s = configs.c1()
+    elif case == "c2_21":
+        s = configs.c2(21)
+    elif case == "p1_128":
+        s = configs.p1(128)
+    else:
+        rp, ci, va = random_csr(4000, 11, long_rows=(5, 2000), long_len=200)
+        s = cd.System(4000, rp, ci, va, np.ones(4000))
+    A, _ = to_dev(g, s)
+    monkeypatch.delenv("GSK_ILU_SWEEP", raising=False)
+    M1 = g.Ilu0(A)
+    monkeypatch.setenv("GSK_ILU_SWEEP", "grid")
+    M2 = g.Ilu0(A)
+    i1, i2 = M1.info(), M2.info()
+    assert i1["one_block"] and not i2["one_block"]
+    assert i1["levels_lower"] == i2["levels_lower"] > 1
+    for seed in (0, 1):
+        r = torch.as_tensor(np.random.default_rng(seed).normal(size=s.n), device="cuda")
+        assert torch.equal(M1.apply(r), M2.apply(r))
+    M1.close()
+    M2.close()
+
+
+def test_large_systems_take_the_grid_sweep():
+    g = gsk()
+    s = configs.c2(40)  # z of 64,000 rows does not fit in one block's shared memory
+    A, _ = to_dev(g, s)
+    M = g.Ilu0(A)
+    assert not M.info()["one_block"]
+    M.close()
