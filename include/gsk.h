@@ -285,8 +285,9 @@ gsk_status gmres_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, i
  *   steps  host: k = m, or fewer when the Krylov space becomes invariant
  *          (h_{k+1,k} <= 1e-14 ||A v_k||, the breakdown rule of gmres_solve);
  *          0 when v0 = 0
- * Runs the solver's kernels from a host loop (one synchronisation per step)
- * and synchronises `stream` before returning.  GSK_ERR_ARG for a non-FP64
+ * Runs the solver's basis kernels as one CUDA graph launch (recorded on the
+ * first call for this matrix, v0 and m, then reused) and synchronises
+ * `stream` before returning.  GSK_ERR_ARG for a non-FP64
  * matrix, m outside 1..64 or a NULL pointer; GSK_ERR_NONFINITE when v0 or A
  * v_j is not finite.
  */

@@ -279,8 +279,10 @@ gsk_status gm_profile(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, in
 }
 
 // The Arnoldi process alone: init (r0 = v0 - A 0 = v0) and m steps of the
-// solver's basis kernels from a host loop, one readback per step; gm_gc
-// records the unrotated Hessenberg columns.  The step loop ends where a GMRES
+// solver's basis kernels, recorded once as a plain graph (no conditional
+// node: as in the solver's unrolled cycle, the steps after the cycle has
+// ended return at entry) and cached per (matrix, v0, m, workspace); gm_gc
+// records the unrotated Hessenberg columns.  The steps end where a GMRES
 // cycle would (k = m or breakdown): tol 0 never ends it, maxit = m.
 static gsk_status gm_arnoldi(gsk_ctx* ctx, const gsk_csr* A, const double* v0, int m, double* H, int* steps,
                              cudaStream_t st) {
@@ -295,22 +297,38 @@ static gsk_status gm_arnoldi(gsk_ctx* ctx, const gsk_csr* A, const double* v0, i
   std::memset(H, 0, hbytes);
   *steps = 0;
   if (A->n == 0) return GSK_OK;
+  P.a.in_graph = 0;  // no conditional handle in this graph
+  P.a.unrolled = 1;
+  std::vector<uint64_t> key = {7, (uint64_t)A->n, (uint64_t)A->nnz, (uint64_t)m, (uint64_t)A->rowptr,
+                               (uint64_t)A->colidx, (uint64_t)A->val, (uint64_t)v0, (uint64_t)ctx->ws};
+  GraphEntry* ge = ctx->find_graph(key);
+  if (!ge) {
+    cudaGraph_t gph = nullptr;
+    GSK_CK(cudaGraphCreate(&gph, 0));
+    struct Guard {
+      cudaGraph_t g;
+      ~Guard() { if (g) cudaGraphDestroy(g); }
+    } guard{gph};
+    cudaStream_t cs = ctx->capture;
+    Capture c0;
+    GSK_CK(c0.begin(cs, gph));
+    gm_launch(ctx, P, kKGmInit, cs);
+    for (int j = 0; j < m; ++j) {
+      gm_launch(ctx, P, kKGmGa, cs);
+      for (int k : {kKGmGd, kKGmGb, kKGmGc}) gm_launch_cgs(P, k, gm_kclass(j + 1), cs);
+    }
+    GSK_CK(c0.end());
+    cudaGraphExec_t ex = nullptr;
+    GSK_CK(cudaGraphInstantiate(&ex, gph, 0));
+    ge = ctx->add_graph(key, ex);
+  }
   if ((s = gm_upload(ctx, P, st)) != GSK_OK) return s;
   GSK_CK(cudaMemsetAsync(P.xzero, 0, sizeof(double) * (size_t)A->n, st));
   GSK_CK(cudaMemsetAsync(P.a.Hraw, 0, hbytes, st));
-  gm_launch(ctx, P, kKGmInit, st);
-  GSK_CK(cudaGetLastError());
+  GSK_CK(cudaGraphLaunch(ge->exec, st));
   GmState S;
   int bits = 0;
   if ((s = gm_readback(ctx, P, st, S, bits)) != GSK_OK) return s;
-  while (!S.stop && !bits) {
-    const int c = gm_kclass(S.j + 1);
-    gm_launch(ctx, P, kKGmGa, st);
-    for (int k : {kKGmGd, kKGmGb, kKGmGc}) gm_launch_cgs(P, k, c, st);
-    GSK_CK(cudaGetLastError());
-    if ((s = gm_readback(ctx, P, st, S, bits)) != GSK_OK) return s;
-    if (!S.cont) break;
-  }
   if ((s = err_bits_status(ctx, bits)) != GSK_OK) return s;
   if (!S.stop) *steps = S.kcols;
   GSK_CK(cudaMemcpyAsync(H, P.a.Hraw, hbytes, cudaMemcpyDeviceToHost, st));
