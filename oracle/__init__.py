@@ -50,9 +50,9 @@ def lib():
         L.or_metric_weights.argtypes = [C.c_int, _ip, _dp, _dp]
         L.or_arnoldi.argtypes = [C.c_int, _ip, _ip, _dp, _dp, C.c_int, _dp, _dp]
         L.or_gmres.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_int, C.c_double,
-                               C.c_int, vp, vp, C.POINTER(_Info), vp]
+                               C.c_int, vp, vp, C.POINTER(_Info), vp, vp, C.c_int]
         L.or_bicgstab.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_double, C.c_int,
-                                  C.c_int, vp, vp, C.POINTER(_Info), vp]
+                                  C.c_int, vp, vp, C.POINTER(_Info), vp, vp, C.c_int]
         L.or_ilu0.argtypes = [C.c_int, _ip, _ip, _dp, _dp]
         L.or_ilu0_apply.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp]
         L.or_ilu0_apply.restype = None
@@ -144,42 +144,62 @@ def ilu0_apply(rowptr, colidx, lu, r):
     return z
 
 
-def gmres(rowptr, colidx, val, b, m=30, tol=1e-8, maxit=10000, x0=None, w=None, history=False, lu=None):
+def gmres(rowptr, colidx, val, b, m=30, tol=1e-8, maxit=10000, x0=None, w=None, history=False, lu=None,
+          trace=False):
     """Restarted GMRES(m) with CGS2, right-preconditioned by ILU(0) factors
-    lu when given; returns (x, info dict[, history])."""
+    lu when given; returns (x, info dict[, history][, cycles]).  With
+    trace=True, cycles is a list of dicts, one per cycle: steps, tau (the
+    least-squares target it ran with), est (its last estimate) and mu (the
+    weighted metric after it)."""
     rowptr, colidx, val = _csr(rowptr, colidx, val)
     n = len(rowptr) - 1
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
     ww = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
     hist = np.full(maxit, np.nan) if history else None
+    cap = maxit + 1
+    tr = np.full(4 * cap, np.nan) if trace else None
     info = _Info()
     lu = None if lu is None else np.ascontiguousarray(lu, dtype=np.float64)
     _check(lib().or_gmres(n, rowptr, colidx, val, b, x, int(m), float(tol), int(maxit),
-                          _ptr(ww), _ptr(lu), C.byref(info), _ptr(hist)))
+                          _ptr(ww), _ptr(lu), C.byref(info), _ptr(hist), _ptr(tr), cap if trace else 0))
     d = info.as_dict()
+    out = [x, d]
     if history:
-        return x, d, hist[: d["iters"]]
-    return x, d
+        out.append(hist[: d["iters"]])
+    if trace:
+        t = tr.reshape(cap, 4)
+        out.append([dict(steps=int(r[0]), tau=float(r[1]), est=float(r[2]), mu=float(r[3]))
+                    for r in t if not np.isnan(r[0])])
+    return tuple(out)
 
 
-def bicgstab(rowptr, colidx, val, b, tol=1e-8, maxit=10000, refresh=3, x0=None, w=None, history=False, lu=None):
+def bicgstab(rowptr, colidx, val, b, tol=1e-8, maxit=10000, refresh=3, x0=None, w=None, history=False, lu=None,
+             trace=False):
     """Bi-CGSTAB with true-residual confirmation, right-preconditioned by
-    ILU(0) factors lu when given; returns (x, info dict[, history])."""
+    ILU(0) factors lu when given; returns (x, info dict[, history][, checks]).
+    With trace=True, checks lists each true-residual confirmation as a dict:
+    iters (the count at that point) and mu (the true metric found)."""
     rowptr, colidx, val = _csr(rowptr, colidx, val)
     n = len(rowptr) - 1
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
     ww = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
     hist = np.full(maxit, np.nan) if history else None
+    cap = int(refresh) + 2
+    tr = np.full(2 * cap, np.nan) if trace else None
     info = _Info()
     lu = None if lu is None else np.ascontiguousarray(lu, dtype=np.float64)
     _check(lib().or_bicgstab(n, rowptr, colidx, val, b, x, float(tol), int(maxit), int(refresh),
-                             _ptr(ww), _ptr(lu), C.byref(info), _ptr(hist)))
+                             _ptr(ww), _ptr(lu), C.byref(info), _ptr(hist), _ptr(tr), cap if trace else 0))
     d = info.as_dict()
+    out = [x, d]
     if history:
-        return x, d, hist[: d["iters"]]
-    return x, d
+        out.append(hist[: d["iters"]])
+    if trace:
+        t = tr.reshape(cap, 2)
+        out.append([dict(iters=int(r[0]), mu=float(r[1])) for r in t if not np.isnan(r[0])])
+    return tuple(out)
 
 
 def relres(rowptr, colidx, val, b, x, x0=None, w=None):

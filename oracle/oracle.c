@@ -319,10 +319,15 @@ int or_arnoldi(int n, const int* rp, const int* ci, const double* va,
  * estimate said "converged" but the weighted metric did not, tau is tightened
  * by tol / metric and the method restarts.
  *
- * hist (optional, length maxit) receives |g_j+1| / ||r0|| per step. */
+ * hist (optional, length maxit) receives |g_j+1| / ||r0|| per step.
+ * trace (optional, 4 * trace_cap doubles) receives one record per cycle:
+ * the steps it took, the tau it ran with, its last estimate |g_j+1| / ||r0||
+ * and the weighted metric after its update of x (records past trace_cap are
+ * dropped).  Neither output changes the arithmetic. */
 int or_gmres(int n, const int* rp, const int* ci, const double* va,
              const double* b, double* x, int m, double tol, int maxit,
-             const double* w_in, const double* lu, or_info* info, double* hist) {
+             const double* w_in, const double* lu, or_info* info, double* hist,
+             double* trace, int trace_cap) {
   memset(info, 0, sizeof(*info));
   if (n <= 0 || m < 1 || maxit < 0 || !(tol >= 0.0)) return OR_ERR_ARG;
   size_t nn = (size_t)n;
@@ -414,6 +419,12 @@ int or_gmres(int n, const int* rp, const int* ci, const double* va,
     residual(n, rp, ci, va, b, x, r);
     double mu = wnorm(n, w, r) / mu0;
     info->relres_true = mu;
+    if (trace && cycle < trace_cap) {
+      trace[4 * cycle + 0] = kcols;
+      trace[4 * cycle + 1] = tau;
+      trace[4 * cycle + 2] = info->relres_rec;
+      trace[4 * cycle + 3] = mu;
+    }
     if (mu < tol) { info->conv = OR_CONVERGED; break; }
     if (info->iters >= maxit || kcols == 0) { info->conv = OR_MAXIT; break; }
     if (est_hit) tau = tau * (tol / mu);
@@ -444,10 +455,15 @@ out:
  * OR_STAGNATED.  An iteration is one pass with two products by A; a half-step
  * exit counts as one iteration.
  *
- * hist (optional, length maxit) receives the recursive metric per iteration. */
+ * hist (optional, length maxit) receives the recursive metric per iteration.
+ * trace (optional, 2 * trace_cap doubles) receives one record per
+ * true-residual confirmation: the iteration count at that point and the
+ * true metric found (records past trace_cap are dropped).  Neither output
+ * changes the arithmetic. */
 int or_bicgstab(int n, const int* rp, const int* ci, const double* va,
                 const double* b, double* x, double tol, int maxit, int refresh,
-                const double* w_in, const double* lu, or_info* info, double* hist) {
+                const double* w_in, const double* lu, or_info* info, double* hist,
+                double* trace, int trace_cap) {
   memset(info, 0, sizeof(*info));
   if (n <= 0 || maxit < 0 || !(tol >= 0.0) || refresh < 0) return OR_ERR_ARG;
   size_t nn = (size_t)n;
@@ -479,7 +495,7 @@ int or_bicgstab(int n, const int* rp, const int* ci, const double* va,
   double mu0 = wnorm(n, w, r);
   info->conv = OR_MAXIT;
   if (mu0 == 0.0) { info->conv = OR_CONVERGED; goto out; }
-  int refresh_left = refresh;
+  int refresh_left = refresh, nconfirm = 0;
   for (;;) { /* (re)start from the current r */
     memcpy(rh, r, sizeof(double) * nn);
     memcpy(p, r, sizeof(double) * nn);
@@ -528,6 +544,11 @@ int or_bicgstab(int n, const int* rp, const int* ci, const double* va,
     /* the recursive residual met tol: confirm with the true residual */
     residual(n, rp, ci, va, b, x, t);
     double mu = wnorm(n, w, t) / mu0;
+    if (trace && nconfirm < trace_cap) {
+      trace[2 * nconfirm + 0] = info->iters;
+      trace[2 * nconfirm + 1] = mu;
+    }
+    nconfirm++;
     if (mu < tol) { info->conv = OR_CONVERGED; info->relres_true = mu; goto out; }
     if (refresh_left == 0) { info->conv = OR_STAGNATED; info->relres_true = mu; goto out; }
     refresh_left--;

@@ -1,0 +1,86 @@
+"""GPU parity of the two solver branches that fire only when the cheap
+convergence estimate and the true residual disagree, against the oracle
+(whose branches are pinned in test_oracle_branches):
+
+* Bi-CGSTAB's true-residual refresh and STAGNATED outcome (Sec. 2.2): on an
+  ill-posed right-hand side the true metric cannot fall below ~5e-11, so at
+  tol = 1e-13 every allowed refresh is taken and the solve ends STAGNATED.
+  The counts at which the confirmations happen move with rounding, so the
+  GPU's iteration count is held to the oracle's rounding ensemble (5%,
+  at least +-2), its refresh count and outcome exactly, and its true metric
+  (recomputed by the oracle from the GPU's x) to the ensemble's range.
+* GMRES(m)'s tightened cycle target: on a row-scaled system the unweighted
+  least-squares estimate meets tol a cycle before the GS(2)-weighted metric
+  of Sec. 2.2 does, so the next cycle runs with tau * tol / metric.  These
+  counts do not move with rounding (the oracle's ensemble has one value),
+  so the GPU must take exactly the oracle's steps and restarts.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from branch_cases import ill_posed_c1, row_scaled_system
+from gpu_util import gsk
+
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(np.float64).eps
+
+
+def _gpu_solve(solver, rp, ci, va, b, tol, m=None, refresh=3, maxit=10000):
+    import torch
+
+    g = gsk()
+    A = g.Csr.from_host(rp, ci, va, device="cuda")
+    bd = torch.as_tensor(b, device="cuda")
+    x = torch.zeros_like(bd)
+    o = g.opts(maxit=maxit, refresh=refresh)
+    if solver == "gmres":
+        info = g.gmres_solve(A, bd, x, m=m, tol=tol, options=o)
+    else:
+        info = g.bicgstab_solve(A, bd, x, tol=tol, options=o)
+    return x.cpu().numpy(), info
+
+
+def _perturbed(b, k):
+    if k == 0:
+        return b
+    return b * (1.0 + np.random.default_rng(k).uniform(-1, 1, len(b)) * EPS)
+
+
+@pytest.mark.parametrize("refresh", [0, 1, 3])
+def test_bicgstab_refresh_and_stagnation_match_the_oracle(refresh):
+    rp, ci, va, b = ill_posed_c1()
+    tol = 1e-13
+    x_g, ig = _gpu_solve("bicgstab", rp, ci, va, b, tol, refresh=refresh)
+    ens = [oracle.bicgstab(rp, ci, va, _perturbed(b, k), tol=tol, refresh=refresh, trace=True) for k in range(8)]
+    its = [e[1]["iters"] for e in ens]
+    mus = [e[1]["relres_true"] for e in ens]
+    msg = f"gpu={ig} oracle iters={its} mu={mus}"
+    assert all(e[1]["conv"] == oracle.STAGNATED and e[1]["refreshes"] == refresh for e in ens)
+    assert ig["conv"] == oracle.STAGNATED, msg
+    assert ig["refreshes"] == refresh, msg
+    lo, hi = min(its), max(its)
+    assert min(0.95 * lo, lo - 2) <= ig["iters"] <= max(1.05 * hi, hi + 2), msg
+    # the true metric of the GPU's x, recomputed by the oracle, is what the
+    # GPU reported and lies in the range the oracle's runs end in
+    mu_g = oracle.relres(rp, ci, va, b, x_g)
+    assert abs(mu_g - ig["relres_true"]) <= 1e-6 * mu_g, msg
+    assert mu_g >= tol and 0.3 * min(mus) <= mu_g <= 3.0 * max(mus), (mu_g, msg)
+    # the recursive metric met tol: this was a refresh/stagnation, not maxit
+    assert ig["relres_rec"] < tol, msg
+
+
+@pytest.mark.parametrize("seed,m", [(11, 20), (3, 20), (29, 20), (3, 40)])
+def test_gmres_tightened_target_matches_the_oracle(seed, m):
+    rp, ci, va, b = row_scaled_system(seed)
+    tol = 1e-10
+    x_o, io, cyc = oracle.gmres(rp, ci, va, b, m=m, tol=tol, maxit=2000, trace=True)
+    assert any(c["est"] < c["tau"] and c["mu"] >= tol for c in cyc), "the case must tighten tau"
+    x_g, ig = _gpu_solve("gmres", rp, ci, va, b, tol, m=m, maxit=2000)
+    msg = f"gpu={ig} oracle={io} cycles={[c['steps'] for c in cyc]}"
+    assert ig["conv"] == oracle.CONVERGED, msg
+    assert ig["iters"] == io["iters"] and ig["restarts"] == io["restarts"], msg
+    mu_g = oracle.relres(rp, ci, va, b, x_g)
+    assert mu_g < tol and abs(mu_g - ig["relres_true"]) <= 1e-6 * mu_g, msg
+    assert np.linalg.norm(x_g - x_o) <= 1e-8 * np.linalg.norm(x_o), msg
