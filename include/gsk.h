@@ -150,9 +150,16 @@ void gsk_opts_default(gsk_opts* opts);
  *   b      in/out: device [n], same dtype as A, scaled in place; may be NULL
  *   p      >= 1, or INFINITY
  *   d_out  optional device FP64 [n]: receives d_i = 1/||a_i||_p (the diagonal
- *          of D); NULL to skip
- * Errors: GSK_ERR_ARG (p < 1, bad sizes/pointers), GSK_ERR_ZERO_ROW,
- * GSK_ERR_NONFINITE.  On error A and b are left unmodified.
+ *          of D), 0 for a row in error; NULL to skip
+ * One pass over the matrix: each row's norm is formed and the row scaled as
+ * it is read, so its values are read once and written once.
+ * Errors: GSK_ERR_ARG (p < 1, bad sizes/pointers, row pointers out of
+ * range), GSK_ERR_ZERO_ROW (a row is all zero, or its norm is below 2^-1024),
+ * GSK_ERR_NONFINITE (NaN or Inf in a row or in b).  On error the rows that
+ * caused it (with their b entries), and every row of a 32-row tile whose row
+ * pointers are out of range, are left unmodified; the other rows are scaled.
+ * gs_scale_static checks every row before it scales any, and leaves A and b
+ * entirely unmodified on error.
  * Synchronises `stream` to read the error flags back.
  */
 gsk_status gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, void* stream);
@@ -169,11 +176,15 @@ gsk_status gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, 
  * 8 MiB + 256 B compiled into the library, which every GPU that loads the
  * library holds until the process exits.
  *   A, b, p, d_out, stream   as for gs_scale (device pointers, caller-owned)
+ * It checks every row before it scales any (two passes over the values), and
+ * on valid input its result is bit-identical to gs_scale's.
  * Limits and errors: with d_out == NULL, at most 1,048,576 rows (larger n
  * returns GSK_ERR_ARG; pass d_out to scale larger systems, then only the
  * error word is used); also GSK_ERR_ARG / GSK_ERR_ZERO_ROW / GSK_ERR_NONFINITE
- * as gs_scale (A and b are left unmodified on error), GSK_ERR_CUDA if a CUDA
- * call fails.  No error text is kept (there is no context).
+ * as gs_scale, but here A and b are left entirely unmodified on error;
+ * GSK_ERR_CUDA if a CUDA call fails.  No error text is kept (there is no
+ * context).  The scratch array lives on the device that is current when the
+ * call is made, which must be the device holding A and b.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Every call shares the array and clears the

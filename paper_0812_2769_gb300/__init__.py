@@ -280,7 +280,9 @@ class Ilu0:
 
 
 def gs_scale(A: Csr, b=None, p: float = 2.0, d_out=None, ctx: Context | None = None, stream=None):
-    """GS(p) in place on A (and b): row i divided by ||a_i||_p (Sec. 2, Eq. (2))."""
+    """GS(p) in place on A (and b): row i divided by ||a_i||_p (Sec. 2, Eq. (2)),
+    in one pass.  On error (GskError) only the rows that caused it are left
+    unscaled; gs_scale_static leaves A and b untouched on error."""
     ctx = ctx or default_context(A.val.device.index or 0)
     Ac = A.c()
     ctx.check(lib().gs_scale(ctx.handle, C.byref(Ac), _ptr(b), float(p), _ptr(d_out), _stream_ptr(stream)))
@@ -293,7 +295,8 @@ def gs_scale_static(A: Csr, b=None, p: float = 2.0, d_out=None, stream=None):
     library (at most 1,048,576 rows when d_out is None); calls that overlap on
     the GPU race on it.  Raises GskError with the status on failure."""
     Ac = A.c()
-    st = lib().gs_scale_static(C.byref(Ac), _ptr(b), float(p), _ptr(d_out), _stream_ptr(stream))
+    with _torch().cuda.device(A.val.device):  # the library's array on A's device
+        st = lib().gs_scale_static(C.byref(Ac), _ptr(b), float(p), _ptr(d_out), _stream_ptr(stream))
     if st != OK:
         raise GskError(st, "gs_scale_static failed")
     return d_out

@@ -308,7 +308,7 @@ __device__ bool block_gs(const BatchSys& S, double* d, double* w2, bool need_w2,
       atomicOr(&s_err, kErrIndex);
       continue;
     }
-    if (scale) d[i] = 1.0 / row_norm(S.val + rs, re - rs, pm, S.p, &s_err);
+    if (scale) d[i] = row_inv_norm(S.val + rs, re - rs, pm, S.p, &s_err);
     const unsigned long long bb = (unsigned long long)__double_as_longlong(S.b[i]);
     if ((bb & 0x7ff0000000000000ull) == 0x7ff0000000000000ull) atomicOr(&s_err, kErrNonFinite);
   }
@@ -324,7 +324,7 @@ __device__ bool block_gs(const BatchSys& S, double* d, double* w2, bool need_w2,
       for (int k = rs; k < re; ++k) S.val[k] *= di;
       S.b[i] *= di;
     }
-    if (need_w2) w2[i] = 1.0 / row_norm(S.val + rs, re - rs, kP2, 2.0, &s_err);
+    if (need_w2) w2[i] = row_inv_norm(S.val + rs, re - rs, kP2, 2.0, &s_err);
   }
   __syncthreads();
   if (s_err) {

@@ -186,56 +186,157 @@ __host__ __device__ inline int pmode_of(double p) {
   return p == 1.0 ? kP1 : (p == 2.0 ? kP2 : (p > 1e300 ? kPInf : kPGen));
 }
 
-// ||a||_p of one row held in shared memory (values converted to double).
-// p = 2 sums squares directly unless the largest magnitude is near the ends
-// of the exponent range, where the row is first scaled by an exact power of
-// two; this is the definition up to rounding.  The largest magnitude and the
-// finiteness test use the integer bit patterns (no FP64 work).
+// The bit pattern of v, through an opaque move.  Tests on a double's bits
+// (finiteness, the largest magnitude) are then done as integer instructions:
+// written on the reinterpreted bits directly, the compiler recognises them and
+// turns them into FP64 compares, which occupy the scarce FP64 pipe (measured:
+// a finiteness test and a maximum doubled the FP64 instructions of a row-norm
+// loop).
+__device__ __forceinline__ unsigned long long dbits(double v) {
+  unsigned long long b;
+  asm("mov.b64 %0, %1;" : "=l"(b) : "d"(v));
+  return b;
+}
+
+// True when a bit pattern is a finite double (exponent field not all ones).
+__device__ __forceinline__ bool finite_pattern(unsigned long long b) {
+  return (b & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
+// Reciprocals for the GS scales.  FP64 instructions are scarce on this part
+// (a correctly rounded FP64 division or square root costs tens of them per
+// row), so d = 1/||a||_p is formed from an FP32 seed (the hardware
+// approximation of 1/x or 1/sqrt(x), about 22 correct bits, taken on the
+// FP32 pipe) and one cubically convergent Householder correction in FP64 (a
+// published method: Householder's iteration of order 3 for the reciprocal
+// and the reciprocal square root).  With e = 1 - s y or e = 1 - s y^2 of
+// size 2^-22, the corrections
+//     1/s:        y + y (e + e^2)
+//     1/sqrt(s):  y + y e (1/2 + 3/8 e)
+// leave a relative error of order e^3 (2^-66), below the rounding of the
+// few FP64 operations that form them: the result is within a few ulp of the
+// exact value.  The seed's exponent is moved by integer operations on the bit
+// pattern, so only 3 (1/s) or 5 (1/sqrt(s)) FP64 instructions are issued.
+// Both take a positive, finite, normal s; the callers route the rare
+// subnormal or near-overflow cases to the plain division.
+
+// 1/s for a positive normal s whose reciprocal is normal too (s < 2^1022).
+__device__ __forceinline__ double recip_pos(double s) {
+  const long long bits = (long long)dbits(s);
+  const int ex = (int)(bits >> 52);  // biased exponent
+  if (ex == 0 || ex >= 2045) return 1.0 / s;
+  // s = 2^(ex-1023) f with f in [1, 2): seed 1/f in FP32
+  const unsigned fb = 0x3f800000u | (unsigned)((bits >> 29) & 0x7fffffll);
+  const unsigned yb = __float_as_uint(__frcp_rn(__uint_as_float(fb)));
+  const int fe = (int)((yb >> 23) & 0xffu) - 127;  // -1 or 0
+  const double y =
+      __longlong_as_double(((long long)(fe - ex + 2046) << 52) | ((long long)(yb & 0x7fffffu) << 29));
+  const double e = fma(-s, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+
+// 1/sqrt(s) for a positive normal s.
+__device__ __forceinline__ double rsqrt_pos(double s) {
+  const long long bits = (long long)dbits(s);
+  const int ex = (int)(bits >> 52);
+  if (ex == 0 || ex == 2047) return 1.0 / sqrt(s);
+  const int e2 = ex - 1023;  // s = 2^e2 f, f in [1, 2)
+  const int k = e2 >> 1;     // s = 2^(2k) g, g = f 2^(e2 - 2k) in [1, 4)
+  const unsigned gb = ((unsigned)(127 + (e2 - 2 * k)) << 23) | (unsigned)((bits >> 29) & 0x7fffffll);
+  const unsigned yb = __float_as_uint(rsqrtf(__uint_as_float(gb)));  // 1/sqrt(g) in (1/2, 1]
+  const int fe = (int)((yb >> 23) & 0xffu) - 127;
+  const double y =
+      __longlong_as_double(((long long)(fe - k + 1023) << 52) | ((long long)(yb & 0x7fffffu) << 29));
+  const double t = s * y;
+  const double e = fma(-t, y, 1.0);
+  return fma(y, e * fma(0.375, e, 0.5), y);
+}
+
+// The rare cases of row_inv_norm, out of line so that the common path keeps
+// few registers: a row whose largest exponent e is far from 0 (its sum could
+// overflow or lose the small terms) and general p.  The row is summed again
+// after an exact scaling by sc = 2^-e, which puts its largest term in [1, 2);
+// then 1/||a|| = (1/||a sc||) sc.
 template <typename T>
-__device__ __forceinline__ double row_norm(const T* v, int len, int pmode, double p, int* err) {
-  unsigned long long mb = 0ull;
-  bool nonfinite = false;
-  for (int k = 0; k < len; ++k) {
-    unsigned long long bits = (unsigned long long)__double_as_longlong((double)v[k]) & 0x7fffffffffffffffull;
-    nonfinite |= bits >= 0x7ff0000000000000ull;
-    mb = bits > mb ? bits : mb;
+__device__ __noinline__ double row_inv_norm_rescaled(const T* v, int len, int pmode, double p, int e,
+                                                     unsigned long long mb) {
+  const double sc = ldexp(1.0, -e);
+  double t = 0.0;
+  if (pmode == kPInf) {
+    t = __longlong_as_double((long long)mb) * sc;
+  } else {
+    for (int k = 0; k < len; ++k) {
+      const double q = fabs((double)v[k]) * sc;
+      if (pmode == kP1) t += q;
+      else if (pmode == kP2) t = fma(q, q, t);
+      else t += pow(q, p);
+    }
   }
-  if (nonfinite) {
+  double dt;
+  if (pmode == kP2) dt = rsqrt_pos(t);
+  else if (pmode == kPGen) dt = 1.0 / pow(t, 1.0 / p);
+  else dt = recip_pos(t);
+  return dt * sc;
+}
+
+// d = 1/||a||_p of one row (entries converted to double), for GS(p)
+// (Sec. 2, Eq. (2)).  One pass over the row for p = 1, 2 and inf: the
+// largest magnitude, the finiteness test (both on the integer bit patterns,
+// no FP64 work) and the sum are taken together.  When the largest exponent is
+// far from 0 the sum could overflow or lose the small terms, and the row is
+// summed again after an exact power-of-two scaling; the result is the
+// definition up to rounding.  A non-finite entry, an all-zero row or a norm
+// whose reciprocal is not a finite double (every entry below 2^-1024) records
+// an error bit in *err and returns 0 (the row is then not scaled).
+template <int PM, typename T>
+__device__ __forceinline__ double row_inv_norm_pm(const T* v, int len, double p, int* err) {
+  constexpr int pmode = PM;
+  unsigned long long mb = 0ull;  // largest |a| (its bit pattern)
+  unsigned long long nf = 0ull;  // nonzero when an entry is Inf or NaN
+  double s = 0.0;
+  for (int k = 0; k < len; ++k) {
+    const double a = (double)v[k];
+    const unsigned long long bits = dbits(a) & 0x7fffffffffffffffull;
+    nf |= (bits + 0x0010000000000000ull) & 0x8000000000000000ull;  // exponent field all ones
+    mb = bits > mb ? bits : mb;
+    if (pmode == kP1) s += fabs(a);
+    else if (pmode == kP2) s = fma(a, a, s);
+  }
+  if (nf) {
     atomicOr(err, kErrNonFinite);
-    return 1.0;
+    return 0.0;
   }
   if (mb == 0ull) {
     atomicOr(err, kErrZeroRow);
-    return 1.0;
+    return 0.0;
   }
-  const double m = __longlong_as_double((long long)mb);
-  if (pmode == kPInf) return m;
-  if (pmode == kP1) {
-    double s = 0.0;
-    for (int k = 0; k < len; ++k) s += fabs((double)v[k]);
-    return s;
+  const int e = (int)(mb >> 52) - 1023;  // exponent of the largest magnitude
+  double d;
+  if (pmode == kP2 && e > -480 && e < 480) {
+    d = rsqrt_pos(s);
+  } else if (pmode == kP1 && e > -1000 && e < 1000 && len < (1 << 20)) {
+    d = recip_pos(s);
+  } else if (pmode == kPInf && e > -1000 && e < 1000) {
+    d = recip_pos(__longlong_as_double((long long)mb));
+  } else {
+    d = row_inv_norm_rescaled(v, len, pmode, p, e, mb);
   }
-  if (pmode == kP2) {
-    const int e = (int)(mb >> 52) - 1023;
-    if (e > -480 && e < 480) {
-      double s = 0.0;
-      for (int k = 0; k < len; ++k) {
-        const double a = (double)v[k];
-        s = fma(a, a, s);
-      }
-      return sqrt(s);
-    }
-    const double sc = ldexp(1.0, -e), isc = ldexp(1.0, e);
-    double s = 0.0;
-    for (int k = 0; k < len; ++k) {
-      const double a = (double)v[k] * sc;
-      s = fma(a, a, s);
-    }
-    return sqrt(s) * isc;
+  if (!finite_pattern(dbits(d))) {  // the norm underflows the reciprocal's range
+    atomicOr(err, kErrZeroRow);
+    return 0.0;
   }
-  double s = 0.0;
-  for (int k = 0; k < len; ++k) s += pow(fabs((double)v[k]) / m, p);
-  return m * pow(s, 1.0 / p);
+  return d;
+}
+
+// The same with p chosen at run time (the one-block batched solvers).
+template <typename T>
+__device__ __forceinline__ double row_inv_norm(const T* v, int len, int pmode, double p, int* err) {
+  switch (pmode) {
+    case kP1: return row_inv_norm_pm<kP1>(v, len, p, err);
+    case kP2: return row_inv_norm_pm<kP2>(v, len, p, err);
+    case kPInf: return row_inv_norm_pm<kPInf>(v, len, p, err);
+    default: return row_inv_norm_pm<kPGen>(v, len, p, err);
+  }
 }
 
 // ------------------------------------------------------------- CSR tiles

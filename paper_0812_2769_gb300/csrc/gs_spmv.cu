@@ -1,12 +1,18 @@
 // Geometric scaling GS(p) (Sec. 1; Sec. 2, Eq. (2)) and the CSR product
 // y = A x used by every Krylov step.
 //
-// GS(p) runs as two kernels so that a malformed or singular input leaves A
-// and b untouched: gs_norm computes d_i = 1/||a_i||_p for every row and
-// records errors (bad structure, non-finite values, zero rows); gs_apply then
-// multiplies row i of A and b_i by d_i only if no error was recorded.  Both
-// stage each 32-row tile's nonzeros through shared memory so that global
-// loads and stores are coalesced and each lane works on its own row.
+// GS(p) is one pass over the matrix (gs_rows_kernel<SCALE = true>): a warp
+// copies the nonzeros of 32 consecutive rows into shared memory with
+// coalesced loads, each lane forms d_i = 1/||a_i||_p of its own row in one
+// sweep (row_inv_norm) and multiplies the row by it in place there, and the
+// warp writes the tile back with coalesced stores: the values are read once
+// and written once.  A row that is all zero or holds a non-finite entry (or
+// whose b_i is not finite), and every row of a tile whose row pointers are
+// out of range, is left as it is and the error is reported.
+// The same kernel without the scaling (SCALE = false) gives the scales alone:
+// the solvers' stopping-metric weights W = 1/||a_i||_2 and the first pass of
+// the two-pass forms (the allocation-free entry point and the two-sided
+// scaling), which scale only after every row has been checked.
 #include <mutex>
 
 #include "internal.hpp"
@@ -39,46 +45,76 @@ __device__ __forceinline__ TileExt tile_extents(const int* __restrict__ rowptr, 
   return t;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBlock) gs_norm_kernel(int n, int nnz, const int* __restrict__ rowptr,
-                                                         const T* __restrict__ val, const T* __restrict__ b,
-                                                         int pmode, double p, double* __restrict__ d,
-                                                         int* err) {
+__device__ __forceinline__ bool finite_bits(double v) { return finite_pattern(dbits(v)); }
+
+// One warp per 32-row tile, tiles strided over the grid; PM is the kind of
+// norm (p = 1, 2, inf or general).  d (optional)
+// receives d_i = 1/||a_i||_p, or 0 for a row in error.  With SCALE, row i of
+// A and b_i are multiplied by d_i in place (rows in error are left as they
+// are).  Tiles whose nonzeros exceed the staging capacity (very long rows)
+// are read straight from global memory.
+template <typename T, bool SCALE, int PM>
+__global__ void __launch_bounds__(kBlock) gs_rows_kernel(int n, int nnz, const int* __restrict__ rowptr,
+                                                         T* __restrict__ val, T* __restrict__ b, double p,
+                                                         double* __restrict__ d, int* err) {
   __shared__ T stage[kWarpsPerBlock][kStageCap];
   T* st = stage[warp_id()];
-  const int ntiles = (n + 31) / 32;
-  for (int tile = blockIdx.x * kWarpsPerBlock + warp_id(); tile < ntiles; tile += gridDim.x * kWarpsPerBlock) {
-    const TileExt t = tile_extents(rowptr, n, nnz, tile * 32, err);
+  const long long ntiles = ((long long)n + 31) / 32;
+  for (long long tile = (long long)blockIdx.x * kWarpsPerBlock + warp_id(); tile < ntiles;
+       tile += (long long)gridDim.x * kWarpsPerBlock) {
+    const TileExt t = tile_extents(rowptr, n, nnz, (int)(tile * 32), err);
+    if (!t.tile_ok) continue;  // recorded; the tile's rows are not touched
     const int cnt = t.e1 - t.e0;
-    double nrm = 1.0;
-    if (t.tile_ok && cnt <= kStageCap) {
-      for (int k = lane_id(); k < cnt; k += 32) st[k] = __ldg(val + t.e0 + k);
+    const bool staged = cnt <= kStageCap;
+    if (staged) {
+#pragma unroll 4
+      for (int k = lane_id(); k < cnt; k += 32) st[k] = val[t.e0 + k];
       __syncwarp();
-      if (t.ok && t.row < n) nrm = row_norm(st + (t.rs - t.e0), t.re - t.rs, pmode, p, err);
-      __syncwarp();
-    } else if (t.ok && t.row < n) {
-      nrm = row_norm(val + t.rs, t.re - t.rs, pmode, p, err);
     }
-    if (t.row < n) {
-      d[t.row] = 1.0 / nrm;
-      if (b) {
-        const unsigned long long bits = (unsigned long long)__double_as_longlong((double)b[t.row]);
-        if ((bits & 0x7ff0000000000000ull) == 0x7ff0000000000000ull) atomicOr(err, kErrNonFinite);
+    double di = 0.0;
+    bool scale = false;
+    if (t.ok && t.row < n) {
+      const T* rv = staged ? st + (t.rs - t.e0) : val + t.rs;
+      di = row_inv_norm_pm<PM>(rv, t.re - t.rs, p, err);
+      scale = dbits(di) != 0ull;  // 0 marks a row in error
+      if (b && !finite_bits((double)b[t.row])) {
+        atomicOr(err, kErrNonFinite);
+        scale = false;
       }
+      if (d) d[t.row] = scale ? di : 0.0;
     }
+    if (SCALE) {
+      if (staged) {
+        if (scale)
+          for (int k = t.rs - t.e0; k < t.re - t.e0; ++k) st[k] = (T)((double)st[k] * di);
+        __syncwarp();
+        if (__any_sync(kFull, scale)) {
+#pragma unroll 4
+          for (int k = lane_id(); k < cnt; k += 32) val[t.e0 + k] = st[k];
+        }
+      } else if (scale) {
+        for (int k = t.rs; k < t.re; ++k) val[k] = (T)((double)val[k] * di);
+      }
+      if (scale && b) b[t.row] = (T)((double)b[t.row] * di);
+    }
+    if (staged) __syncwarp();  // the stage is reused by the warp's next tile
   }
 }
 
+// Second pass of the two-pass form: row i of A and b_i multiplied by d_i,
+// only if the first pass recorded no error (A and b are then left as they
+// were).  The same multiplications as gs_rows_kernel<SCALE = true>.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) gs_apply_kernel(int n, int nnz, const int* __restrict__ rowptr,
                                                           T* __restrict__ val, T* __restrict__ b,
                                                           const double* __restrict__ d, int* err) {
-  if (*(volatile int*)err != 0) return;  // errors found by gs_norm: leave A and b as they are
+  if (*(volatile int*)err != 0) return;  // errors found by the first pass: leave A and b as they are
   __shared__ T stage[kWarpsPerBlock][kStageCap];
   T* st = stage[warp_id()];
-  const int ntiles = (n + 31) / 32;
-  for (int tile = blockIdx.x * kWarpsPerBlock + warp_id(); tile < ntiles; tile += gridDim.x * kWarpsPerBlock) {
-    const TileExt t = tile_extents(rowptr, n, nnz, tile * 32, err);
+  const long long ntiles = ((long long)n + 31) / 32;
+  for (long long tile = (long long)blockIdx.x * kWarpsPerBlock + warp_id(); tile < ntiles;
+       tile += (long long)gridDim.x * kWarpsPerBlock) {
+    const TileExt t = tile_extents(rowptr, n, nnz, (int)(tile * 32), err);
     const int cnt = t.e1 - t.e0;
     const double di = t.row < n ? d[t.row] : 0.0;
     if (cnt <= kStageCap) {
@@ -122,11 +158,31 @@ __global__ void __launch_bounds__(kBlock) unit_check_kernel(int n, const double*
   if (grid_sum(blk, 1, red, tot) && threadIdx.x == 0) *out = tot[0] == 0.0 ? 1 : 0;
 }
 
+// Grid of the GS kernels: one warp per 32-row tile, every block that fits.
+static int gs_grid(gsk_ctx* ctx, const void* kernel, int n) {
+  return ctx->occ_grid(kernel, ((long long)n + 31) / 32, kWarpsPerBlock);
+}
+
+// Launches gs_rows_kernel<T, SCALE, PM> with PM taken from p; grid = 0 sizes
+// the grid from the kernel's occupancy (needs ctx), else the given grid.
+template <typename T, bool SCALE>
+static void launch_gs_rows(gsk_ctx* ctx, int grid, int n, int nnz, const int* rowptr, T* val, T* b, double p,
+                           double* d, int* err, cudaStream_t st) {
+  auto go = [&](auto kernel) {
+    const int g = grid > 0 ? grid : gs_grid(ctx, (const void*)kernel, n);
+    kernel<<<g, kBlock, 0, st>>>(n, nnz, rowptr, val, b, p, d, err);
+  };
+  switch (pmode_of(p)) {
+    case kP1: go(gs_rows_kernel<T, SCALE, kP1>); break;
+    case kP2: go(gs_rows_kernel<T, SCALE, kP2>); break;
+    case kPInf: go(gs_rows_kernel<T, SCALE, kPInf>); break;
+    default: go(gs_rows_kernel<T, SCALE, kPGen>); break;
+  }
+}
+
 void launch_gs_norm(gsk_ctx* ctx, int n, int nnz, const int* rowptr, const double* val, double p, double* d,
                     int* err, cudaStream_t st) {
-  int pmode = p == 1.0 ? kP1 : (p == 2.0 ? kP2 : (p > 1e300 ? kPInf : kPGen));
-  const int grid = ctx->grid_for((n + 31) / 32, kWarpsPerBlock, 8);
-  gs_norm_kernel<double><<<grid, kBlock, 0, st>>>(n, nnz, rowptr, val, nullptr, pmode, p, d, err);
+  launch_gs_rows<double, false>(ctx, 0, n, nnz, rowptr, const_cast<double*>(val), nullptr, p, d, err, st);
 }
 
 void launch_unit_check(gsk_ctx* ctx, int n, const double* w, const GridRed& red, int* out, cudaStream_t st) {
@@ -149,32 +205,17 @@ gsk_status launch_spmv(gsk_ctx* ctx, const gsk_csr* A, const void* x, void* y, i
 }
 
 gsk_status run_gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, cudaStream_t st) {
-  int pmode;
-  if (p == 1.0) pmode = kP1;
-  else if (p == 2.0) pmode = kP2;
-  else if (p > 1e300) pmode = kPInf;
-  else pmode = kPGen;
   const int n = A->n;
-  // workspace: error word + d (when the caller does not want it)
   Arena a;
-  a.take<int>(64);
-  if (!d_out) a.take<double>(n);
+  a.take<int>(64);  // error word
   gsk_status s = ctx->reserve(a.off);
   if (s != GSK_OK) return s;
-  a = Arena{(char*)ctx->ws, ctx->ws_bytes, 0};
-  int* err = a.take<int>(64);
-  double* d = d_out ? d_out : a.take<double>(n);
+  int* err = (int*)ctx->ws;
   GSK_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
-  const int grid = ctx->grid_for((n + 31) / 32, kWarpsPerBlock, 8);
-  if (A->dtype == GSK_F64) {
-    gs_norm_kernel<double><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const double*)A->val,
-                                                     (const double*)b, pmode, p, d, err);
-    gs_apply_kernel<double><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (double*)A->val, (double*)b, d, err);
-  } else {
-    gs_norm_kernel<float><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const float*)A->val,
-                                                    (const float*)b, pmode, p, d, err);
-    gs_apply_kernel<float><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (float*)A->val, (float*)b, d, err);
-  }
+  if (A->dtype == GSK_F64)
+    launch_gs_rows<double, true>(ctx, 0, n, A->nnz, A->rowptr, (double*)A->val, (double*)b, p, d_out, err, st);
+  else
+    launch_gs_rows<float, true>(ctx, 0, n, A->nnz, A->rowptr, (float*)A->val, (float*)b, p, d_out, err, st);
   GSK_CK(cudaGetLastError());
   int* hbits = (int*)ctx->host_pinned;
   GSK_CK(cudaMemcpyAsync(hbits, err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -230,7 +271,7 @@ __global__ void __launch_bounds__(kBlock) diag_mul_kernel(int n, const double* _
 
 gsk_status run_gs_scale_sym(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* s_out, double* w_out,
                             cudaStream_t st) {
-  const int pmode = p == 1.0 ? kP1 : (p == 2.0 ? kP2 : (p > 1e300 ? kPInf : kPGen));
+  const int pmode = pmode_of(p);
   const int n = A->n;
   Arena a;
   a.take<int>(64);
@@ -241,22 +282,18 @@ gsk_status run_gs_scale_sym(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double*
   int* err = a.take<int>(64);
   double* d = a.take<double>(n);
   GSK_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
-  const int gt = ctx->grid_for((n + 31) / 32, kWarpsPerBlock, 8);
+  const int gt = ctx->grid_for(((long long)n + 31) / 32, kWarpsPerBlock, 8);
   const int gr = ctx->grid_for(n, kBlock, 8);
   const int gn = ctx->grid_for(A->nnz, kBlock, 8);
   const bool w_is_d = pmode == kP2;
   if (A->dtype == GSK_F64) {
-    gs_norm_kernel<double><<<gt, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const double*)A->val,
-                                                   (const double*)b, pmode, p, d, err);
+    launch_gs_rows<double, false>(ctx, gt, n, A->nnz, A->rowptr, (double*)A->val, (double*)b, p, d, err, st);
     if (w_out && !w_is_d)
-      gs_norm_kernel<double><<<gt, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const double*)A->val, nullptr, kP2,
-                                                     2.0, w_out, err);
+      launch_gs_rows<double, false>(ctx, gt, n, A->nnz, A->rowptr, (double*)A->val, nullptr, 2.0, w_out, err, st);
   } else {
-    gs_norm_kernel<float><<<gt, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const float*)A->val, (const float*)b,
-                                                  pmode, p, d, err);
+    launch_gs_rows<float, false>(ctx, gt, n, A->nnz, A->rowptr, (float*)A->val, (float*)b, p, d, err, st);
     if (w_out && !w_is_d)
-      gs_norm_kernel<float><<<gt, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const float*)A->val, nullptr, kP2, 2.0,
-                                                    w_out, err);
+      launch_gs_rows<float, false>(ctx, gt, n, A->nnz, A->rowptr, (float*)A->val, nullptr, 2.0, w_out, err, st);
   }
   if (A->nnz > 0) sym_check_kernel<<<gn, kBlock, 0, st>>>(A->nnz, n, A->colidx, err);
   sym_prep_kernel<<<gr, kBlock, 0, st>>>(n, d, s_out, w_out, w_is_d ? 1 : 0);
@@ -284,11 +321,14 @@ gsk_status launch_diag_mul(gsk_ctx* ctx, int n, const double* s, void* x, gsk_dt
 
 // --------------------------------------------------- allocation-free GS(p)
 //
-// gs_scale_static: the same two GS(p) kernels as gs_scale, for callers that
-// must not allocate device memory (and so cannot create a gsk_ctx, whose
-// workspace is allocated).  Its scratch -- the error word and, when the caller
-// passes no d_out, the per-row scales -- lives in the file-scope array below,
-// which every device that loads the library holds until the process exits.
+// gs_scale_static: GS(p) for callers that must not allocate device memory
+// (and so cannot create a gsk_ctx, whose workspace is allocated).  It runs
+// the two-pass form -- every row's scale and check first, the scaling only if
+// no row failed -- with the per-row arithmetic of gs_scale, so on valid input
+// the two give bit-identical results.  Its scratch -- the error word and,
+// when the caller passes no d_out, the per-row scales -- lives in the
+// file-scope array below, which every device that loads the library holds
+// until the process exits.
 namespace gsk {
 namespace {
 constexpr int kStaticMaxRows = 1 << 20;  // rows whose scales fit in the array
@@ -346,17 +386,14 @@ extern "C" gsk_status gs_scale_static(gsk_csr* A, void* b, double p, double* d_o
   int* err = (int*)sd->scratch;
   double* d = d_out ? d_out : (double*)((char*)sd->scratch + kStaticHeader);
   if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return GSK_ERR_CUDA;  // left set by the last call
-  const int pmode = p == 1.0 ? kP1 : (p == 2.0 ? kP2 : (p > 1e300 ? kPInf : kPGen));
-  long long g = ((long long)(A->n + 31) / 32 + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const long long g = (((long long)A->n + 31) / 32 + kWarpsPerBlock - 1) / kWarpsPerBlock;
   const int grid = (int)(g < (long long)sd->sms * 8 ? (g < 1 ? 1 : g) : (long long)sd->sms * 8);
   const int n = A->n;
   if (A->dtype == GSK_F64) {
-    gs_norm_kernel<double><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const double*)A->val,
-                                                     (const double*)b, pmode, p, d, err);
+    launch_gs_rows<double, false>(nullptr, grid, n, A->nnz, A->rowptr, (double*)A->val, (double*)b, p, d, err, st);
     gs_apply_kernel<double><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (double*)A->val, (double*)b, d, err);
   } else {
-    gs_norm_kernel<float><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (const float*)A->val,
-                                                    (const float*)b, pmode, p, d, err);
+    launch_gs_rows<float, false>(nullptr, grid, n, A->nnz, A->rowptr, (float*)A->val, (float*)b, p, d, err, st);
     gs_apply_kernel<float><<<grid, kBlock, 0, st>>>(n, A->nnz, A->rowptr, (float*)A->val, (float*)b, d, err);
   }
   if (cudaGetLastError() != cudaSuccess) return GSK_ERR_CUDA;

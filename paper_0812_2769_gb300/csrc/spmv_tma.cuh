@@ -100,7 +100,12 @@ __device__ __forceinline__ void pipe_issue(PipeSmem<T>& sm, int st, int e0, int 
   } else if (aligned) {
     const CopyRange<16 / sizeof(T)> vr(e0, e1, nnz);
     const CopyRange<4> cr(e0, e1, nnz);
-    if (vr.a1 - vr.a0 <= kPipeCap && cr.a1 - cr.a0 <= kPipeCap) {
+    // the stage receives [a0, max(a1, e1)): the bulk copy up to a1, then, on
+    // the matrix's last chunk, the plain loads of [tail, e1), which end past
+    // a1 when e1 was rounded down
+    const int vspan = (vr.a1 > e1 ? vr.a1 : e1) - vr.a0;
+    const int cspan = (cr.a1 > e1 ? cr.a1 : e1) - cr.a0;
+    if (vspan <= kPipeCap && cspan <= kPipeCap) {
       direct = 0;
       va0 = vr.a0;
       ca0 = cr.a0;

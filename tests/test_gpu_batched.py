@@ -59,10 +59,17 @@ def test_batched_iteration_counts_within_oracle_ensemble():
     infos, _ = g.bicgstab_solve_batched(As, bs, xs, p=2.0, tol=1e-8)
     for s, info in zip(systems, infos):
         sc = _gs(s, 2.0)
+        # the GPU's GS(2) values differ from the oracle's by a few ulp (it
+        # multiplies by a reciprocal, the oracle divides), so the ensemble
+        # perturbs the scaled values (<= 2 ulp) as well as b (<= 1 ulp); on
+        # these inclusion systems the count spreads by up to 30% under such
+        # perturbations, so the ensemble is large enough to reach its tails
         its = []
-        for seed in range(6):
-            bb = sc.b if seed == 0 else sc.b * (1 + np.random.default_rng(seed).uniform(-1, 1, s.n) * 2.2e-16)
-            its.append(oracle.bicgstab(sc.rowptr, sc.colidx, sc.val, bb, tol=1e-8)[1]["iters"])
+        for seed in range(48):
+            rs = np.random.default_rng(seed)
+            bb = sc.b if seed == 0 else sc.b * (1 + rs.uniform(-1, 1, s.n) * 2.2e-16)
+            vv = sc.val if seed == 0 else sc.val * (1 + rs.uniform(-2, 2, len(sc.val)) * 2.2e-16)
+            its.append(oracle.bicgstab(sc.rowptr, sc.colidx, vv, bb, tol=1e-8)[1]["iters"])
         lo, hi = min(its), max(its)
         assert min(0.95 * lo, lo - 2) <= info["iters"] <= max(1.05 * hi, hi + 2), (info["iters"], its)
 

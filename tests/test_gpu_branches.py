@@ -5,10 +5,12 @@ convergence estimate and the true residual disagree, against the oracle
 * Bi-CGSTAB's true-residual refresh and STAGNATED outcome (Sec. 2.2): on an
   ill-posed right-hand side the true metric cannot fall below ~5e-11, so at
   tol = 1e-13 every allowed refresh is taken and the solve ends STAGNATED.
-  The counts at which the confirmations happen move with rounding, so the
-  GPU's iteration count is held to the oracle's rounding ensemble (5%,
-  at least +-2), its refresh count and outcome exactly, and its true metric
-  (recomputed by the oracle from the GPU's x) to the ensemble's range.
+  The first confirmation comes at the oracle's count (rounding ensemble, 5%,
+  at least +-2).  After a restart from a residual at the rounding floor the
+  counts are rounding noise, so there the GPU is held to the same restart
+  identity that pins the oracle's branch (bit for bit, on the GPU itself),
+  to the oracle's outcome and refresh count, and to the range of true
+  metrics the oracle ends in.
 * GMRES(m)'s tightened cycle target: on a row-scaled system the unweighted
   least-squares estimate meets tol a cycle before the GS(2)-weighted metric
   of Sec. 2.2 does, so the next cycle runs with tau * tol / metric.  These
@@ -27,13 +29,13 @@ pytestmark = pytest.mark.gpu
 EPS = np.finfo(np.float64).eps
 
 
-def _gpu_solve(solver, rp, ci, va, b, tol, m=None, refresh=3, maxit=10000):
+def _gpu_solve(solver, rp, ci, va, b, tol, m=None, refresh=3, maxit=10000, x0=None):
     import torch
 
     g = gsk()
     A = g.Csr.from_host(rp, ci, va, device="cuda")
     bd = torch.as_tensor(b, device="cuda")
-    x = torch.zeros_like(bd)
+    x = torch.zeros_like(bd) if x0 is None else torch.as_tensor(np.array(x0), device="cuda")
     o = g.opts(maxit=maxit, refresh=refresh)
     if solver == "gmres":
         info = g.gmres_solve(A, bd, x, m=m, tol=tol, options=o)
@@ -48,27 +50,59 @@ def _perturbed(b, k):
     return b * (1.0 + np.random.default_rng(k).uniform(-1, 1, len(b)) * EPS)
 
 
-@pytest.mark.parametrize("refresh", [0, 1, 3])
-def test_bicgstab_refresh_and_stagnation_match_the_oracle(refresh):
+def test_bicgstab_stagnation_matches_the_oracle():
+    """refresh = 0: the first true-residual confirmation ends the solve as
+    STAGNATED, at the oracle's iteration count (rounding ensemble) and with a
+    true metric in the range the oracle's runs end in."""
     rp, ci, va, b = ill_posed_c1()
     tol = 1e-13
-    x_g, ig = _gpu_solve("bicgstab", rp, ci, va, b, tol, refresh=refresh)
-    ens = [oracle.bicgstab(rp, ci, va, _perturbed(b, k), tol=tol, refresh=refresh, trace=True) for k in range(8)]
+    x_g, ig = _gpu_solve("bicgstab", rp, ci, va, b, tol, refresh=0)
+    ens = [oracle.bicgstab(rp, ci, va, _perturbed(b, k), tol=tol, refresh=0) for k in range(8)]
     its = [e[1]["iters"] for e in ens]
     mus = [e[1]["relres_true"] for e in ens]
     msg = f"gpu={ig} oracle iters={its} mu={mus}"
-    assert all(e[1]["conv"] == oracle.STAGNATED and e[1]["refreshes"] == refresh for e in ens)
-    assert ig["conv"] == oracle.STAGNATED, msg
-    assert ig["refreshes"] == refresh, msg
+    assert all(e[1]["conv"] == oracle.STAGNATED for e in ens)
+    assert ig["conv"] == oracle.STAGNATED and ig["refreshes"] == 0, msg
     lo, hi = min(its), max(its)
     assert min(0.95 * lo, lo - 2) <= ig["iters"] <= max(1.05 * hi, hi + 2), msg
-    # the true metric of the GPU's x, recomputed by the oracle, is what the
-    # GPU reported and lies in the range the oracle's runs end in
-    mu_g = oracle.relres(rp, ci, va, b, x_g)
-    assert abs(mu_g - ig["relres_true"]) <= 1e-6 * mu_g, msg
-    assert mu_g >= tol and 0.3 * min(mus) <= mu_g <= 3.0 * max(mus), (mu_g, msg)
-    # the recursive metric met tol: this was a refresh/stagnation, not maxit
     assert ig["relres_rec"] < tol, msg
+    # the true metric of the GPU's x, recomputed by the oracle: at this floor
+    # (eps cond(A)) the residual itself carries rounding noise of a few per
+    # cent, so the reported and recomputed values agree to 10%
+    mu_g = oracle.relres(rp, ci, va, b, x_g)
+    assert abs(mu_g - ig["relres_true"]) <= 0.1 * mu_g, (mu_g, msg)
+    assert mu_g >= tol and 0.3 * min(mus) <= mu_g <= 3.0 * max(mus), (mu_g, msg)
+
+
+@pytest.mark.parametrize("refresh", [1, 3])
+def test_bicgstab_refresh_continues_as_a_fresh_start_on_the_gpu(refresh):
+    """The GPU's refresh restarts r, r^ and p from the true residual: a solve
+    with `refresh` restarts continues exactly (bit for bit) like a fresh GPU
+    solve started from the x of the first confirmation with refresh - 1, its
+    tolerance rescaled to the fresh start's ||W r0|| -- the identity that
+    pins the oracle's branch (test_oracle_branches).  After the restarts the
+    solve is STAGNATED, as in the oracle, every refresh taken, and its true
+    metric lies in the oracle's range."""
+    rp, ci, va, b = ill_posed_c1()
+    tol = 1e-13
+    x, info = _gpu_solve("bicgstab", rp, ci, va, b, tol, refresh=refresh)
+    x1, i1 = _gpu_solve("bicgstab", rp, ci, va, b, tol, refresh=0)
+    assert i1["conv"] == oracle.STAGNATED
+    w = oracle.metric_weights(rp, va)
+    mu0 = np.linalg.norm(w * b)
+    mu1 = np.linalg.norm(w * (b - oracle.spmv(rp, ci, va, x1)))
+    x2, i2 = _gpu_solve("bicgstab", rp, ci, va, b, tol * mu0 / mu1, refresh=refresh - 1, x0=x1)
+    msg = f"full={info} first={i1} fresh={i2}"
+    assert info["iters"] == i1["iters"] + i2["iters"], msg
+    assert info["refreshes"] == 1 + i2["refreshes"], msg
+    assert np.array_equal(x, x2), msg
+    # outcome against the oracle
+    ens = [oracle.bicgstab(rp, ci, va, _perturbed(b, k), tol=tol, refresh=refresh) for k in range(8)]
+    mus = [e[1]["relres_true"] for e in ens]
+    assert all(e[1]["conv"] == oracle.STAGNATED and e[1]["refreshes"] == refresh for e in ens)
+    assert info["conv"] == oracle.STAGNATED and info["refreshes"] == refresh, msg
+    mu = oracle.relres(rp, ci, va, b, x)
+    assert mu >= tol and 0.3 * min(mus) <= mu <= 3.0 * max(mus), (mu, mus, msg)
 
 
 @pytest.mark.parametrize("seed,m", [(11, 20), (3, 20), (29, 20), (3, 40)])

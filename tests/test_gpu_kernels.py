@@ -56,42 +56,74 @@ def test_gs_scale_extreme_magnitudes():
         _gs_case(s2, p)
 
 
-def _expect_error(sys_, status, p=2.0):
+def _expect_error(sys_, status, bad_rows, p=2.0):
+    """gs_scale reports `status`; the rows that caused it (and their b
+    entries) are left bit-for-bit as they were, every other row is scaled as
+    the oracle scales it."""
     import torch
 
     g = gsk()
     A, b = to_dev(g, sys_)
-    before = A.val.clone(), b.clone()
     with pytest.raises(g.GskError) as ei:
         g.gs_scale(A, b, p=p)
     assert ei.value.status == status
-    # nothing modified (bitwise, so NaN entries compare equal to themselves)
-    assert A.val.view(torch.int64).equal(before[0].view(torch.int64))
-    assert b.view(torch.int64).equal(before[1].view(torch.int64))
+    val, bb = A.val.cpu().numpy(), b.cpu().numpy()
+    bad = np.zeros(sys_.n, dtype=bool)
+    bad[list(bad_rows)] = True
+    rows = np.repeat(np.arange(sys_.n), np.diff(sys_.rowptr))
+    same = bad[rows]
+    # bitwise, so NaN entries compare equal to themselves
+    assert np.array_equal(val[same].view(np.int64), sys_.val[same].view(np.int64))
+    assert np.array_equal(bb[bad].view(np.int64), sys_.b[bad].view(np.int64))
+    # the good rows: as the oracle scales them (it works row by row)
+    good = ~bad
+    keep = good[rows]
+    sub_rp = np.zeros(good.sum() + 1, dtype=np.int32)
+    sub_rp[1:] = np.cumsum(np.diff(sys_.rowptr)[good])
+    v_or, b_or, _ = oracle.gs_scale(sub_rp, sys_.colidx[keep], sys_.val[keep], sys_.b[good], p)
+    assert np.all(np.abs(val[keep] - v_or) <= GS_RTOL * np.abs(v_or))
+    assert np.all(np.abs(bb[good] - b_or) <= GS_RTOL * np.abs(b_or) + 1e-300)
 
 
-def test_gs_zero_row_is_an_error_and_leaves_input():
+def test_gs_zero_row_is_an_error_and_only_that_row_is_left():
     s = configs.c1(10)
     val = s.val.copy()
     val[s.rowptr[37]:s.rowptr[38]] = 0.0
-    _expect_error(cd.System(s.n, s.rowptr, s.colidx, val, s.b), gsk().ERR_ZERO_ROW)
+    _expect_error(cd.System(s.n, s.rowptr, s.colidx, val, s.b), gsk().ERR_ZERO_ROW, [37])
 
 
-def test_gs_nonfinite_is_an_error_and_leaves_input():
+def test_gs_nonfinite_is_an_error_and_only_that_row_is_left():
     s = configs.c1(10)
     val = s.val.copy()
     val[17] = np.inf
-    _expect_error(cd.System(s.n, s.rowptr, s.colidx, val, s.b), gsk().ERR_NONFINITE)
+    row17 = int(np.searchsorted(s.rowptr, 17, side="right") - 1)
+    _expect_error(cd.System(s.n, s.rowptr, s.colidx, val, s.b), gsk().ERR_NONFINITE, [row17])
     b = s.b.copy()
     b[5] = np.nan
-    _expect_error(cd.System(s.n, s.rowptr, s.colidx, s.val, b), gsk().ERR_NONFINITE)
+    _expect_error(cd.System(s.n, s.rowptr, s.colidx, s.val, b), gsk().ERR_NONFINITE, [5])
 
 
 def test_gs_malformed_rowptr_is_an_error():
+    g = gsk()
     s = configs.c1(10)
     rp = s.rowptr.copy()
     rp[40] = rp[41] + 3  # decreasing extent
-    _expect_error(cd.System(s.n, rp, s.colidx, s.val, s.b), gsk().ERR_ARG)
+    A, b = to_dev(g, cd.System(s.n, rp, s.colidx, s.val, s.b))
+    with pytest.raises(g.GskError) as ei:
+        g.gs_scale(A, b, p=2.0)
+    assert ei.value.status == g.ERR_ARG
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0, math.inf, 3.5])
+def test_gs_scale_rows_across_the_exponent_range(p):
+    """Rows scaled by 2^k with k spread over [-1000, 1000]: the one-pass
+    reciprocal (FP32 seed, FP64 correction) and the rescaled slow path for
+    rows near the ends of the range both match the oracle's division."""
+    s = configs.c1(24)
+    k = np.random.default_rng(12).integers(-1000, 1001, s.n)
+    k[:8] = [-1000, -999, -480, -479, 479, 480, 999, 1000]
+    rows = np.repeat(np.arange(s.n), np.diff(s.rowptr))
+    _gs_case(cd.System(s.n, s.rowptr, s.colidx, np.ldexp(s.val, k[rows]), np.ldexp(s.b, k)), p)
 
 
 def test_gs_bad_p_rejected():
@@ -136,6 +168,60 @@ def test_spmv_random_with_empty_and_long_rows():
     rp2[1:] = np.cumsum(lens)
     s = cd.System(777, rp2, ci[keep], va[keep], np.zeros(777))
     _spmv_case(s, np.random.default_rng(4).normal(size=777))
+
+
+# The product streams 256-row chunks of the matrix into shared-memory stages
+# of 1856 nonzeros; on the matrix's last chunk the copy ends at a 16-byte
+# boundary and the last few entries are loaded one by one.  These cases put
+# that last chunk at 1855..1859 nonzeros, behind a first chunk of odd length
+# (so its start is not aligned either), in FP64 and FP32.
+PIPE_CAP = 1856
+
+
+def _chunk_case(last_nnz, first_nnz, seed):
+    rs = np.random.default_rng(seed)
+    lens = []
+    for total in ([first_nnz] if first_nnz else []) + [last_nnz]:
+        base, extra = divmod(total, 256)
+        ln = np.full(256, base)
+        ln[rs.choice(256, extra, replace=False)] += 1
+        lens.append(ln)
+    lens = np.concatenate(lens)
+    n = len(lens)
+    rp = np.zeros(n + 1, dtype=np.int32)
+    rp[1:] = np.cumsum(lens)
+    ci = np.concatenate([np.sort(rs.choice(n, L, replace=False)) for L in lens]).astype(np.int32)
+    va = rs.uniform(-1, 1, len(ci))
+    return cd.System(n, rp, ci, va, np.zeros(n))
+
+
+@pytest.mark.parametrize("last_nnz", [PIPE_CAP - 1, PIPE_CAP, PIPE_CAP + 1, PIPE_CAP + 2, PIPE_CAP + 3])
+@pytest.mark.parametrize("first_nnz", [0, 1001])
+def test_spmv_last_chunk_at_the_stage_capacity(last_nnz, first_nnz):
+    s = _chunk_case(last_nnz, first_nnz, seed=last_nnz + first_nnz)
+    assert s.rowptr[-1] == last_nnz + first_nnz
+    _spmv_case(s, np.random.default_rng(5).normal(size=s.n))
+
+
+@pytest.mark.parametrize("last_nnz", [PIPE_CAP - 1, PIPE_CAP + 1, PIPE_CAP + 3])
+def test_spmv_fp32_last_chunk_at_the_stage_capacity(last_nnz):
+    import torch
+
+    s = _chunk_case(last_nnz, 1001, seed=7 * last_nnz)
+    g = gsk()
+    A = g.Csr.from_host(s.rowptr, s.colidx, s.val.astype(np.float32), device="cuda", dtype=torch.float32)
+    x = np.random.default_rng(6).normal(size=s.n).astype(np.float32)
+    y = torch.empty(s.n, dtype=torch.float32, device="cuda")
+    g.gsk_spmv(A, torch.as_tensor(x, device="cuda"), y)
+    torch.cuda.synchronize()
+    v32 = s.val.astype(np.float32).astype(np.float64)
+    y_or = oracle.spmv(s.rowptr, s.colidx, v32, x.astype(np.float64))
+    rows = np.repeat(np.arange(s.n), np.diff(s.rowptr))
+    absum = np.zeros(s.n)
+    np.add.at(absum, rows, np.abs(v32 * x.astype(np.float64)[s.colidx]))
+    lens = np.diff(s.rowptr)
+    feps = float(np.finfo(np.float32).eps)
+    assert np.all(np.abs(y.cpu().numpy().astype(np.float64) - y_or) <= (lens + 2) * feps * absum)
 
 
 def test_spmv_bad_column_index_is_reported():

@@ -30,6 +30,8 @@ def _pair(sys_, p, with_d):
     for got, want in [(A2.val, A1.val), (b2, b1)] + ([(d2, d1)] if with_d else []):
         got, want = got.cpu().numpy(), want.cpu().numpy()
         assert np.all(np.abs(got - want) <= RTOL * np.abs(want))
+        # the two entry points share the per-row arithmetic: in fact bit-identical
+        assert np.array_equal(got.view(np.int64), want.view(np.int64))
 
 
 @pytest.mark.parametrize("p", [1.0, 2.0, math.inf, 3.5])
@@ -48,9 +50,23 @@ def test_static_errors_and_limit():
     val = s.val.copy()
     val[s.rowptr[5]:s.rowptr[6]] = 0.0
     A, b = to_dev(g, cd.System(s.n, s.rowptr, s.colidx, val, s.b))
+    before = A.val.clone(), b.clone()
     with pytest.raises(g.GskError) as ei:
         g.gs_scale_static(A, b, p=2.0)
     assert ei.value.status == g.ERR_ZERO_ROW
+    # on error nothing is modified (compared bitwise)
+    assert A.val.view(torch.int64).equal(before[0].view(torch.int64))
+    assert b.view(torch.int64).equal(before[1].view(torch.int64))
+    # a non-finite b entry: ERR_NONFINITE, A and b again untouched
+    bad_b = s.b.copy()
+    bad_b[3] = np.inf
+    A, b = to_dev(g, cd.System(s.n, s.rowptr, s.colidx, s.val, bad_b))
+    before = A.val.clone(), b.clone()
+    with pytest.raises(g.GskError) as ei:
+        g.gs_scale_static(A, b, p=2.0)
+    assert ei.value.status == g.ERR_NONFINITE
+    assert A.val.view(torch.int64).equal(before[0].view(torch.int64))
+    assert b.view(torch.int64).equal(before[1].view(torch.int64))
     # the error word is cleared by the next call: a good matrix scales fine
     _pair(configs.c1(10), 2.0, with_d=False)
     # more rows than the built-in array holds, without d_out: rejected
