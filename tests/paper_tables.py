@@ -1,6 +1,8 @@
 """Test helper: the paper's printed iteration tables for Problem 1 (Sec. 3,
-Tables 1 and 1a), read from the fixture tests/golden/table1_p1_iterations.txt,
-and the bands within which a run counts as matching them.
+Tables 1 and 1a) and Problem 4 (Sec. 6, Table 4 and the "limit" table),
+read from the fixtures tests/golden/table1_p1_iterations.txt and
+tests/golden/table4_p4_iterations.txt, and the bands within which a run
+counts as matching them.
 
 An entry is an int (iterations to reach the tolerance), "noconv" (no
 convergence within 10,000 iterations) or ("stag", r) (restarted GMRES
@@ -22,14 +24,34 @@ def _entry(tok: str):
     return int(tok)
 
 
+FIXTURE4 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table4_p4_iterations.txt")
+CONVECTIONS = (100.0, 200.0, 500.0, 1000.0)
+
+
 def load(path: str = FIXTURE) -> list[dict]:
+    """Iteration-table rows (Tables 1, 1a and 4)."""
     rows = []
     for ln in open(path):
         if not ln.strip() or ln.startswith("#"):
             continue
         t = ln.split()
+        if t[0] == "limit":
+            continue
         rows.append({"table": t[0], "case": t[1], "solver": t[2], "m": None if t[3] == "-" else int(t[3]),
                      "scaling": t[4], "precond": t[5], "entries": dict(zip(TOLS, (_entry(x) for x in t[6:9])))})
+    return rows
+
+
+def load_limit(path: str = FIXTURE4) -> list[dict]:
+    """Rows of the "limit" table (Sec. 6): the best goal reached (a tolerance
+    of TOLS, or None) per convection strength."""
+    rows = []
+    for ln in open(path):
+        t = ln.split()
+        if not t or t[0] != "limit":
+            continue
+        rows.append({"solver": t[1], "m": None if t[2] == "-" else int(t[2]), "scaling": t[3], "precond": t[4],
+                     "best": dict(zip(CONVECTIONS, (None if x == "none" else float(x) for x in t[5:9])))})
     return rows
 
 
