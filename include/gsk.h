@@ -308,10 +308,26 @@ gsk_status gsk_arnoldi(gsk_ctx* ctx, const gsk_csr* A, const double* v0, int m, 
 /*
  * bicgstab_solve -- Bi-CGSTAB (Sec. 2; van der Vorst 1992) with breakdown
  * tolerance 1e-16 * DBL_EPSILON relative to the vector norms (Sec. 2.2) and
- * true-residual confirmation.  Arguments as for gmres_solve.
+ * true-residual confirmation.  Arguments as for gmres_solve.  Systems of at
+ * most gsk_small_system_rows rows (FP64, no preconditioner) run on one
+ * thread-block cluster; the decisions are the same, the dot products are
+ * summed in another order.
  */
 gsk_status bicgstab_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, double tol,
                           const gsk_opts* opts, gsk_info* info, void* stream);
+
+/*
+ * gsk_small_system_rows -- the largest system (rows) that bicgstab_solve runs
+ * on one thread-block cluster of this context's device: 16 CTAs holding the
+ * iteration vectors in their shared memory, the whole solve in one launch
+ * with no kernel boundary per iteration.  FP64 solves without a
+ * preconditioner of systems this small take that path; larger ones, and every
+ * other solve, the grid-wide solver.  0 when the device cannot launch the
+ * cluster.  The environment variable GSK_SMALL_N, read when a context is
+ * created, lowers the limit (0 turns the path off).  Host pointer; GSK_ERR_ARG
+ * for a NULL argument.
+ */
+gsk_status gsk_small_system_rows(gsk_ctx* ctx, int* rows);
 
 /*
  * bicgstab_solve_batched -- GS(p) then Bi-CGSTAB (Sec. 2) on nsys independent

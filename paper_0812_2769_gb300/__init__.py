@@ -94,6 +94,7 @@ SIGNATURES = {
     "bicgstab_solve": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_void_p, C.c_double,
                         C.POINTER(OptsC), C.POINTER(InfoC), C.c_void_p], C.c_int),
     "gsk_workspace_bytes": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+    "gsk_small_system_rows": ([C.c_void_p, C.POINTER(C.c_int)], C.c_int),
     "gsk_kernel_name": ([C.c_int], C.c_char_p),
     "bicgstab_solve_batched": ([C.c_void_p, C.c_int, C.POINTER(CsrC), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                 C.POINTER(C.c_double), C.c_double, C.POINTER(OptsC), C.POINTER(InfoC),
@@ -449,6 +450,15 @@ def profile_solve(A: Csr, b, x, solver: str = "bicgstab", m: int = 30, tol: floa
                                       C.byref(info), _stream_ptr(stream)))
     out = [(lib().gsk_kernel_name(r.kernel).decode(), r.step, r.ms) for r in recs[: nrec.value]]
     return out, info.as_dict()
+
+
+def small_system_rows(ctx: Context | None = None) -> int:
+    """The largest system bicgstab_solve runs on one thread-block cluster (0:
+    the path is off or unavailable)."""
+    ctx = ctx or default_context(0)
+    out = C.c_int()
+    ctx.check(lib().gsk_small_system_rows(ctx.handle, C.byref(out)))
+    return int(out.value)
 
 
 def workspace_bytes(n: int, nnz: int, solver: str = "bicgstab", m: int = 30, precision: int = PREC_F64) -> int:

@@ -227,6 +227,12 @@ extern "C" gsk_status bicgstab_solve(gsk_ctx* ctx, const gsk_csr* A, const void*
   else gsk_opts_default(&opts);
   if (opts.precision == GSK_PREC_MIXED) return bicgstab_solve_mixed(ctx, A, b, x, tol, &opts, info, stream);
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    // small systems: the whole solve on one thread-block cluster
+    bool used = false;
+    s = bcg_cluster_solve(ctx, A, b, x, tol, opts, info, st, &used);
+    if (used) return s;
+  }
   BcgPlan P;
   if ((s = bcg_prepare(ctx, A, b, x, tol, opts, P)) != GSK_OK) return s;
   if (A->n == 0) {

@@ -75,6 +75,10 @@ gsk_status gsk_ctx_create(gsk_ctx** out, int device) {
     const int k = std::atoi(v);
     if (k >= 1 && k <= 32) ctx->basis_per_sm = k;
   }
+  if (const char* v = std::getenv("GSK_SMALL_N")) {
+    const int k = std::atoi(v);
+    if (k >= 0) ctx->small_n = k;
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);

@@ -52,6 +52,12 @@ struct gsk_ctx {
   // more resident blocks hide less latency than they cost, as the second CGS
   // pass re-reads the basis rows of the first from L1 (measured best: 3)
   int basis_per_sm = 3;
+  // Bi-CGSTAB on one thread-block cluster for systems of at most small_n rows
+  // (GSK_SMALL_N overrides; 0 disables); cluster_max_n: the most rows the
+  // cluster kernel holds on this device (-1: not yet queried)
+  int small_n = 32768;
+  int cluster_max_n = -1;
+  int cluster_smem = 0;  // shared memory per CTA of the cluster kernel
   std::string last_error;
   // device workspace
   void* ws = nullptr;
@@ -193,6 +199,8 @@ struct LaunchTimer {
   }
 };
 
+gsk_status bcg_cluster_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, double tol,
+                             const gsk_opts& opts, gsk_info* info, cudaStream_t st, bool* used);
 gsk_status bcg_profile(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, double tol, const gsk_opts& opts,
                        int max_iters, LaunchTimer& T, gsk_info* info);
 gsk_status gm_profile(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, int m, double tol,

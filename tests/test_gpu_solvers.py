@@ -12,8 +12,10 @@ cond(A) * tol; the test uses ||x_gpu - x_or|| <= max(1e-6, 4 cond_est * tol)
 The rounding ensemble: on these discontinuous systems the Krylov iteration
 count is sensitive to rounding (the oracle itself moves by 20-80% when b is
 perturbed by one ulp), and the GPU necessarily sums in another order.  So
-the oracle is run on b and on seven copies of b perturbed by at most one ulp
-per entry, and the GPU count must lie in [0.95 min, 1.05 max] of those counts.
+the oracle is run on b and on 47 copies of b perturbed by at most one ulp
+per entry, and the GPU count must lie in [0.95 min, 1.05 max] of those counts
+(on unscaled C1 the ensemble spans 1359..2362 iterations; a handful of
+members would miss its tails).
 Where the iteration is stable the ensemble has one value and the bar is the
 plain 5%.
 """
@@ -62,7 +64,7 @@ def _oracle(solver, sys_, b, tol, m, maxit):
     return oracle.bicgstab(sys_.rowptr, sys_.colidx, sys_.val, b, tol=tol, maxit=maxit)
 
 
-def _ensemble(solver, sys_, tol, m, maxit, size=8):
+def _ensemble(solver, sys_, tol, m, maxit, size=48):
     """Oracle runs on b and on size-1 copies of b perturbed by <= 1 ulp."""
     out = [_oracle(solver, sys_, sys_.b, tol, m, maxit)]
     for seed in range(1, size):
