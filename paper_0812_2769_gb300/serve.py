@@ -63,9 +63,9 @@ class Result:
         return self.t_done - self.t_arrival
 
 
-def footprint_bytes(req: Request, workspace_fn=None) -> int:
-    """Device bytes a request holds while it runs: its CSR, b and x, and the
-    solver workspace."""
+def footprint_parts(req: Request, workspace_fn=None) -> tuple[int, int]:
+    """(bytes of the request's own arrays: CSR, b and x; bytes of solver
+    workspace it needs)."""
     s = req.system
     n, nnz = s.n, int(s.rowptr[-1])
     own = 4 * (n + 1) + 12 * nnz + 16 * n
@@ -74,7 +74,20 @@ def footprint_bytes(req: Request, workspace_fn=None) -> int:
     else:
         vec = 4 if req.precision == "mixed" else 8
         ws = (vec * n * (req.m + 2) if req.solver == "gmres" else 8 * vec * n) + 24 * n + 4 * nnz + (1 << 20)
+    return own, ws
+
+
+def footprint_bytes(req: Request, workspace_fn=None) -> int:
+    """Device bytes a request holds while it runs: its CSR, b and x, and the
+    solver workspace."""
+    own, ws = footprint_parts(req, workspace_fn)
     return own + ws
+
+
+def retained_workspace(ws: int) -> int:
+    """What a library context holds after a solve that needed ws bytes of
+    workspace: it grows its workspace to ws + ws/8 + 1 MiB and keeps it."""
+    return ws + ws // 8 + (1 << 20)
 
 
 class GpuBackend:
@@ -93,6 +106,11 @@ class GpuBackend:
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
         self.bctx = g.Context(device)
         self.bstream = torch.cuda.Stream(device=device)
+
+    def trim_slot(self, slot: int):
+        """Free an idle slot's workspace (a new, empty context)."""
+        self.ctxs[slot].close()
+        self.ctxs[slot] = self.g.Context(self.device)
 
     def workspace(self, n, nnz, solver, m, precision):
         g = self.g
@@ -142,7 +160,16 @@ class GpuBackend:
 
 
 class Server:
-    """Admission by HBM footprint, a slot lane and a continuous batch lane."""
+    """Admission by HBM footprint, a slot lane and a continuous batch lane.
+
+    Device memory is accounted as the library holds it: a request's own arrays
+    (CSR, b, x) while it runs; for the slot lane, each slot's context keeps
+    the workspace its largest solve so far needed (a context grows its
+    workspace and does not shrink it), so a request is assigned a slot at
+    admission and counted by how much it would grow that slot's workspace;
+    the batch lane's requests count their workspace while they run.  When the
+    head of the queue does not fit, the workspaces of idle slots are freed
+    first (the backend's trim_slot, if it has one)."""
 
     def __init__(self, backend, slots: int = 4, budget_bytes: int | None = None, small_n: int = 65536,
                  batch_max: int = 256):
@@ -158,9 +185,11 @@ class Server:
         self.batch_max = batch_max
         self.lock = threading.Condition()
         self.pending: deque = deque()  # arrived, not yet admitted (FIFO)
-        self.slot_q: deque = deque()  # admitted, waiting for a slot worker
+        self.slot_q = [deque() for _ in range(slots)]  # admitted, assigned to a slot
         self.batch_q: deque = deque()  # admitted, waiting for the next batch launch
-        self.in_use = 0
+        self.in_use = 0  # running requests' arrays, and the batch lane's workspace
+        self.slot_ws = [0] * slots  # workspace each slot's context holds
+        self.slot_busy = [False] * slots
         self.peak_in_use = 0
         self.free_slots = slots
         self.batch_busy = False
@@ -175,49 +204,91 @@ class Server:
     def _now(self):
         return time.perf_counter() - self.t0
 
+    def resident(self) -> int:
+        """Device bytes the server's requests and slot contexts hold now."""
+        return self.in_use + sum(self.slot_ws)
+
     # -------- admission (called with the lock held)
+    def _pick_slot(self, need: int):
+        """The idle slot a request needing `need` bytes of workspace grows the
+        least, and by how much."""
+        best, grow = None, None
+        for k in range(self.nslots):
+            if self.slot_busy[k]:
+                continue
+            g = max(0, retained_workspace(need) - self.slot_ws[k]) if need > self.slot_ws[k] else 0
+            if grow is None or g < grow:
+                best, grow = k, g
+        return best, grow
+
+    def _trim_idle(self, keep: int | None) -> bool:
+        trim = getattr(self.backend, "trim_slot", None)
+        freed = False
+        for k in range(self.nslots):
+            if k != keep and not self.slot_busy[k] and self.slot_ws[k] > 0:
+                if trim is not None:
+                    trim(k)
+                self.slot_ws[k] = 0
+                freed = True
+        return freed
+
     def _admit(self):
         while self.pending:
             req, t_arr = self.pending[0]
-            fp = footprint_bytes(req, self.workspace_fn)
-            if fp > self.budget:  # can never fit: reject
+            own, ws = footprint_parts(req, self.workspace_fn)
+            lane = self.lane_of(req)
+            total = own + (retained_workspace(ws) if lane == "slot" else ws)
+            if total > self.budget:  # can never fit: reject
                 self.pending.popleft()
                 self.results[req.rid] = Result(req.rid, None, {}, -1, "rejected", t_arr, self._now(), self._now())
                 continue
-            lane = self.lane_of(req)
-            if self.in_use + fp > self.budget:
-                break  # FIFO: wait for memory to free up
-            if lane == "slot" and self.free_slots == 0:
-                break
-            self.pending.popleft()
-            self.in_use += fp
-            self.peak_in_use = max(self.peak_in_use, self.in_use)
             if lane == "slot":
+                if self.free_slots == 0:
+                    break
+                k, grow = self._pick_slot(ws)
+                if self.resident() + own + grow > self.budget:
+                    if self._trim_idle(keep=k):
+                        continue  # try again with the idle slots' workspaces freed
+                    break  # FIFO: wait for memory to free up
+                self.pending.popleft()
+                self.in_use += own
+                if ws > self.slot_ws[k]:
+                    self.slot_ws[k] = retained_workspace(ws)
+                self.slot_busy[k] = True
                 self.free_slots -= 1
-                self.slot_q.append((req, t_arr, self._now(), fp))
+                self.slot_q[k].append((req, t_arr, self._now(), own))
             else:
-                self.batch_q.append((req, t_arr, self._now(), fp))
+                if self.resident() + own + ws > self.budget:
+                    if self._trim_idle(keep=None):
+                        continue
+                    break
+                self.pending.popleft()
+                self.in_use += own + ws
+                self.batch_q.append((req, t_arr, self._now(), own + ws))
+            self.peak_in_use = max(self.peak_in_use, self.resident())
             self.lock.notify_all()
 
-    def _finish(self, req, t_arr, t_adm, fp, x, info, status, lane):
+    def _finish(self, req, t_arr, t_adm, fp, x, info, status, lane, slot=None):
         with self.lock:
             self.results[req.rid] = Result(req.rid, x, info, status, lane, t_arr, t_adm, self._now())
             self.in_use -= fp
             if lane == "slot":
                 self.free_slots += 1
+                self.slot_busy[slot] = False
             self._admit()
             self.lock.notify_all()
 
     def _slot_worker(self, slot: int):
+        q = self.slot_q[slot]
         while True:
             with self.lock:
-                while not self.slot_q and not self.done:
+                while not q and not self.done:
                     self.lock.wait(0.05)
-                if not self.slot_q:
+                if not q:
                     return
-                req, t_arr, t_adm, fp = self.slot_q.popleft()
+                req, t_arr, t_adm, fp = q.popleft()
             x, info, status = self.backend.run_single(slot, req)
-            self._finish(req, t_arr, t_adm, fp, x, info, status, "slot")
+            self._finish(req, t_arr, t_adm, fp, x, info, status, "slot", slot)
 
     def _batch_worker(self):
         while True:
@@ -266,11 +337,21 @@ class Server:
 
 
 def summarize(results: list[Result]) -> dict:
-    ok = [r for r in results if r.status == 0]
-    lat = np.array([r.latency for r in ok]) if ok else np.array([math.nan])
+    """Throughput and latency of a run.  The headline counts only the solves
+    that converged (reached tol): solves that stopped at maxit finished
+    without the accuracy asked for and are reported apart.  Percentiles come
+    with their sample size (p99 of n < 100 samples is an order statistic near
+    the maximum)."""
+    done = [r for r in results if r.status == 0]
+    conv = [r for r in done if r.info.get("conv") == 0]
     span = (max(r.t_done for r in results) - min(r.t_arrival for r in results)) if results else math.nan
-    conv = sum(1 for r in ok if r.info.get("conv") == 0)
-    return {"requests": len(results), "completed": len(ok), "converged": conv,
-            "solves_per_s": len(ok) / span if span > 0 else math.nan,
-            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+
+    def pct(rs, q):
+        return float(np.percentile([r.latency for r in rs], q)) if rs else math.nan
+
+    return {"requests": len(results), "completed": len(done), "converged": len(conv),
+            "solves_per_s": len(conv) / span if span > 0 else math.nan,
+            "p50_s": pct(conv, 50), "p99_s": pct(conv, 99), "latency_samples": len(conv),
+            "completed_per_s": len(done) / span if span > 0 else math.nan,
+            "p50_completed_s": pct(done, 50), "p99_completed_s": pct(done, 99),
             "lanes": {ln: sum(1 for r in results if r.lane == ln) for ln in ("slot", "batch", "rejected")}}

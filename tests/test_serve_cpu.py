@@ -98,3 +98,59 @@ def test_requests_arriving_during_a_batch_join_a_later_launch():
     assert len(be.batches) > 1  # continuous: several launches, not one queue drained at the end
     assert sorted(sum(be.batches, [])) == list(range(30))
     assert any(len(b) > 1 for b in be.batches)  # and arrivals were grouped
+
+
+class TrimBackend(FakeBackend):
+    def __init__(self):
+        super().__init__()
+        self.trims = []
+
+    def trim_slot(self, slot):
+        self.trims.append(slot)
+
+
+def test_slot_workspace_is_counted_until_trimmed():
+    """A slot's context keeps the workspace of its largest solve: the server
+    counts it after the request finishes, and frees idle slots' workspace
+    when the head of the queue would not fit otherwise."""
+    be = TrimBackend()
+    big = serve.Request(0, _sys(120), solver="gmres", m=40)
+    small = [serve.Request(i, _sys(40), solver="gmres", m=20, arrival=0.0) for i in range(1, 6)]
+    own_b, ws_b = serve.footprint_parts(big)
+    own_s, ws_s = serve.footprint_parts(small[0])
+    # room for the big request's retained workspace plus one small request at
+    # a time in a second slot, but not for two retained big workspaces
+    budget = own_b + serve.retained_workspace(ws_b) + own_s + serve.retained_workspace(ws_s) + 1
+    srv = serve.Server(be, slots=2, budget_bytes=budget, small_n=0)
+    res = srv.run([big] + small, realtime=False)
+    assert all(r.status == 0 for r in res)
+    assert srv.peak_in_use <= budget
+    assert srv.in_use == 0
+    # the slots still hold their workspaces after the run; their sum is what
+    # the resident count reports
+    assert srv.resident() == sum(srv.slot_ws) > 0
+
+
+def test_trim_frees_idle_slots_for_a_request_that_needs_the_room():
+    be = TrimBackend()
+    a = serve.Request(0, _sys(100), solver="gmres", m=30)
+    b = serve.Request(1, _sys(100), solver="gmres", m=30, arrival=0.0)
+    own, ws = serve.footprint_parts(a)
+    budget = own + serve.retained_workspace(ws) + own // 2  # one retained workspace at a time
+    srv = serve.Server(be, slots=2, budget_bytes=budget, small_n=0)
+    res = srv.run([a, b], realtime=False)
+    assert all(r.status == 0 for r in res)
+    assert srv.peak_in_use <= budget
+    # the second request went to the slot that already held the workspace,
+    # or an idle slot was trimmed to make room
+    assert sum(1 for w in srv.slot_ws if w > 0) == 1 or be.trims
+
+
+def test_summary_counts_converged_solves_only():
+    mk = lambda rid, conv, t: serve.Result(rid, None, {"conv": conv}, 0, "slot", 0.0, 0.0, t)
+    res = [mk(0, 0, 1.0), mk(1, 0, 2.0), mk(2, 1, 4.0), mk(3, 0, 3.0)]
+    s = serve.summarize(res)
+    assert s["completed"] == 4 and s["converged"] == 3 and s["latency_samples"] == 3
+    assert abs(s["solves_per_s"] - 3 / 4.0) < 1e-12
+    assert abs(s["completed_per_s"] - 4 / 4.0) < 1e-12
+    assert s["p99_s"] <= 3.0 < s["p99_completed_s"]
