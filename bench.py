@@ -59,8 +59,10 @@ def parse_args(argv=None):
                     help="skip the mixed-precision, batched (4096 systems) and serving measurements")
     ap.add_argument("--batch", type=int, default=4096, help="systems in the batched measurement")
     ap.add_argument("--serve-requests", type=int, default=120, help="requests in the serving measurement")
-    ap.add_argument("--profile-kernels", choices=["gmres", "bicgstab", "both"], default=None,
-                    help="only drive the solvers' kernels from a host loop on the workload (for ncu captures)")
+    ap.add_argument("--profile-kernels", choices=["gmres", "bicgstab", "both", "gs"], default=None,
+                    help="only drive the solvers' kernels (or GS(p) alone) on the workload (for ncu captures)")
+    ap.add_argument("--gs-calls", type=int, default=3, help="GS(p) calls per p in --profile-kernels gs")
+    ap.add_argument("--gs-p", type=float, nargs="+", default=[2.0], help="the p of --profile-kernels gs")
     ap.add_argument("--gmres-iters", type=int, default=30, help="Arnoldi steps in --profile-kernels")
     ap.add_argument("--bicgstab-iters", type=int, default=20, help="Bi-CGSTAB iterations in --profile-kernels")
     ap.add_argument("--serial-solves", action="store_true",
@@ -221,28 +223,29 @@ def kernel_cost(name, step, n, nnz):
 
 # The sources that make the kernels of the traffic table and their launch
 # shapes: the two solvers' translation units, everything they include, and
-# the context (grid sizing).  Any edit to one of them voids the recorded
-# traffic; the batched, mixed, GS and ILU sources do not enter.
+# the context (grid sizing); for GS(p), its translation unit.  Any edit to
+# one of them voids the recorded traffic of those kernels (the ABI header,
+# declarations only, does not enter).
 TRAFFIC_SOURCES = ("gmres.cu", "bicgstab.cu", "ctx.cu", "gmres_kernels.cuh", "bicgstab_kernels.cuh", "spmv_tma.cuh",
                    "device_common.cuh", "internal.hpp", "graph.hpp", "ilu.cuh")
+GS_SOURCES = ("gs_spmv.cu", "ctx.cu", "device_common.cuh", "internal.hpp")
 
 
-def source_hash():
+def source_hash(files=TRAFFIC_SOURCES):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_0812_2769_gb300", "csrc")
-    for fn in TRAFFIC_SOURCES:
+    for fn in files:
         h.update(open(os.path.join(d, fn), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "gsk.h"), "rb").read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel):
+def recorded_traffic(kernel, files=TRAFFIC_SOURCES):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
-    want = source_hash()
+    want = source_hash(files)
     for ln in open(path):
         p = ln.split()
         if len(p) >= 3 and not ln.startswith("#") and p[0] == kernel and p[2] == want:
@@ -410,7 +413,7 @@ def run_gpu(args):
 
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
-        cpu = cpu_sample(s)
+        cpu = cpu_sample(args.grid)
 
     extra = None
     if not args.no_extra and rank == 0:
@@ -422,6 +425,7 @@ def run_gpu(args):
         extra["ilu0"] = ilu_pass(g, ctx, A, val0, b, b0, s)
         extra["c1_32"] = c1_pass(g)
         extra["c2_scalings"] = c2_scalings_pass(g, ctx, A, val0, b, b0)
+        extra["gs_scale_128"] = gs_pass(g, ctx, A, val0, b, b0, s)
 
     if rank == 0:
         # per-solve times from the serial steps (alone on the GPU, so per
@@ -453,6 +457,14 @@ def run_gpu(args):
                                "unit": "GB/s", "frac": extra["c3_256"]["spmv"]["f64"]["frac_of_measured_hbm"],
                                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
                               if extra and "c3_256" in extra else None),
+            # GS(2) alone on the benchmark system (from forms.gs_scale_128)
+            "roofline_gs": ({"kernel": "gs_rows_kernel (one pass), 128^3, p = 2", "bound": "hbm",
+                             "achieved": extra["gs_scale_128"]["p2"]["GBps"], "peak": _peaks().get("hbm_gbs"),
+                             "unit": "GB/s", "frac": extra["gs_scale_128"]["p2"]["frac_of_measured_hbm"],
+                             "avg_us": extra["gs_scale_128"]["p2"]["us"],
+                             "traffic": recorded_traffic("gs_rows_p2", GS_SOURCES),
+                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+                            if extra and "gs_scale_128" in extra else None),
             "forms": extra,
         }
         print(json.dumps(line), flush=True)
@@ -613,6 +625,19 @@ def c3_pass(g, steps=2000):
                       "frac_of_measured_hbm": round(byt / us / 1e3 / hbm, 3)}
         del xv, yv
     out["spmv"] = spmv
+    # what the oracle reaches on the same system (written by
+    # tests/golden/make_c3_oracle_trace.py): GMRES(30)'s metric after its first
+    # two cycles, and Bi-CGSTAB over a rounding ensemble (none converges to
+    # 1e-10 within 3,000 iterations)
+    tr = os.path.join(ROOT, "tests", "golden", "c3_oracle_trace.json")
+    if os.path.exists(tr):
+        d = json.load(open(tr))
+        out["oracle"] = {"gmres30_metric_after_cycles": [c["mu"] for c in d["gmres30"]["cycles"]],
+                         "bicgstab_members": len(d["bicgstab"]),
+                         "bicgstab_outcomes": sorted({r["conv"] for r in d["bicgstab"]}),
+                         "bicgstab_metric_range": [min(r["relres_true"] for r in d["bicgstab"]),
+                                                   max(r["relres_true"] for r in d["bicgstab"])],
+                         "bicgstab_maxit": max(r["iters"] for r in d["bicgstab"])}
     del A, val0, b0, b, x
     torch.cuda.empty_cache()
     return out
@@ -626,7 +651,9 @@ def _peaks():
 def c1_pass(g):
     """The 32^2 configuration: latency-bound (the system fits in L2), so
     microseconds per solve rather than a bandwidth fraction: GMRES(20) and
-    Bi-CGSTAB, unscaled and after GS(2), to 1e-8."""
+    Bi-CGSTAB, unscaled and after GS(2), to 1e-8.  Bi-CGSTAB on a system this
+    small runs on one thread-block cluster; it is timed on the grid-wide path
+    too (a context created with GSK_SMALL_N=0)."""
     import torch
 
     from problems import configs
@@ -638,18 +665,27 @@ def c1_pass(g):
     b = b0.clone()
     x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
     ctx = g.Context(torch.cuda.current_device())
-    out = {"n": s.n, "nnz": s.nnz}
+    old = os.environ.get("GSK_SMALL_N")
+    os.environ["GSK_SMALL_N"] = "0"
+    try:
+        ctx_grid = g.Context(torch.cuda.current_device())
+    finally:
+        if old is None:
+            del os.environ["GSK_SMALL_N"]
+        else:
+            os.environ["GSK_SMALL_N"] = old
+    out = {"n": s.n, "nnz": s.nnz, "cluster_path_rows": g.small_system_rows(ctx)}
     for scaled in (False, True):
         A.val.copy_(val0)
         b.copy_(b0)
         if scaled:
             g.gs_scale(A, b, p=2.0, ctx=ctx)
-        for solver in ("gmres20", "bicgstab"):
+        for solver in ("gmres20", "bicgstab", "bicgstab_grid_wide"):
             def solve():
                 x.zero_()
                 if solver == "gmres20":
                     return g.gmres_solve(A, b, x, m=20, tol=TOL, ctx=ctx)
-                return g.bicgstab_solve(A, b, x, tol=TOL, ctx=ctx)
+                return g.bicgstab_solve(A, b, x, tol=TOL, ctx=ctx_grid if solver.endswith("wide") else ctx)
             for _ in range(3):
                 info = solve()
             torch.cuda.synchronize()
@@ -659,7 +695,9 @@ def c1_pass(g):
             dt = (time.perf_counter() - t0) / 20
             out[("gs2_" if scaled else "unscaled_") + solver] = {
                 "us_per_solve": round(1e6 * dt, 1), "solves_per_s": round(1 / dt, 1), "iters": info["iters"],
+                "us_per_iter": round(1e6 * dt / max(info["iters"], 1), 2),
                 "conv_name": info["conv_name"], "relres_true": info["relres_true"]}
+    ctx_grid.close()
     return out
 
 
@@ -763,8 +801,13 @@ def serving_pass(args):
     """Serving: mixed 2D/3D requests (see problems/serving.py), mixed
     precision to 1e-8.  The capacity is measured with every request queued at
     once; then the same requests arrive as a Poisson stream at 50%, 80% and
-    95% of it, each run reporting p50/p99 latency (arrival to completion) and
-    completed solves per second."""
+    95% of it, each run reporting p50/p99 latency (arrival to completion) over
+    the converged solves, with the sample count.  Beside it, the same queued
+    requests through the same server in FP64, and through a plain loop of FP64
+    calls (upload, GS, solve, read back x; one context, one stream)."""
+    import torch
+
+    import paper_0812_2769_gb300 as g
     from paper_0812_2769_gb300 import serve
     from problems import serving as sv
 
@@ -772,24 +815,85 @@ def serving_pass(args):
     specs = sv.stream(n, rate=1.0, seed=7)
     systems = [sp.build() for sp in specs]
 
-    def requests(rate):
+    def requests(rate, precision="mixed"):
         # the stream's request mix does not depend on its rate, only the arrival times
         arr = [sp.arrival for sp in sv.stream(n, rate=rate, seed=7)] if rate else [0.0] * n
-        return [serve.Request(sp.rid, sysm, solver=sp.solver, m=sp.m, p=sp.p, tol=TOL, precision="mixed",
+        return [serve.Request(sp.rid, sysm, solver=sp.solver, m=sp.m, p=sp.p, tol=TOL, precision=precision,
                               arrival=t, maxit=3000) for sp, sysm, t in zip(specs, systems, arr)]
 
     be = serve.GpuBackend(0, slots=6)
     serve.Server(be, slots=6).run(requests(None)[:3], realtime=False)  # warm the contexts
     sat = serve.summarize(serve.Server(be, slots=6).run(requests(None), realtime=False))
     capacity = sat["solves_per_s"]
+    sat64 = serve.summarize(serve.Server(be, slots=6).run(requests(None, "f64"), realtime=False))
     loads = {}
     for f in (0.5, 0.8, 0.95):
         srv = serve.Server(be, slots=6)
         out = serve.summarize(srv.run(requests(f * capacity), realtime=True))
         out.update({"arrival_rate_per_s": round(f * capacity, 3), "peak_admitted_GB": round(srv.peak_in_use / 1e9, 3)})
         loads[f"{round(100 * f)}%"] = out
+
+    # the plain FP64 loop: what a caller without the server does per request
+    ctx = g.Context(0)
+    o = g.opts(precision=g.PREC_F64, maxit=3000)
+    conv = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for sp, sysm in zip(specs, systems):
+        A = g.Csr.from_host(sysm.rowptr, sysm.colidx, sysm.val)
+        b = torch.as_tensor(sysm.b, device="cuda")
+        x = torch.zeros(sysm.n, dtype=torch.float64, device="cuda")
+        g.gs_scale(A, b, p=sp.p, ctx=ctx)
+        if sp.solver == "gmres":
+            info = g.gmres_solve(A, b, x, m=sp.m, tol=TOL, options=o, ctx=ctx)
+        else:
+            info = g.bicgstab_solve(A, b, x, tol=TOL, options=o, ctx=ctx)
+        x.cpu()
+        conv += info["conv"] == g.CONVERGED
+    t_loop = time.perf_counter() - t0
+    ctx.close()
+    keys = ("completed", "converged", "solves_per_s", "p50_s", "p99_s", "latency_samples", "lanes")
     return {"requests_per_run": n, "slots": 6, "maxit": 3000, "capacity_solves_per_s": capacity,
-            "capacity_run": {k: sat[k] for k in ("completed", "converged", "p50_s", "p99_s")}, "loads": loads}
+            "capacity_run": {k: sat[k] for k in keys},
+            "fp64_server": {k: sat64[k] for k in keys},
+            "fp64_loop": {"converged": int(conv), "solves_per_s": conv / t_loop, "seconds": round(t_loop, 3),
+                          "note": "one request after another: upload, GS, FP64 solve, read back x"},
+            "loads": loads}
+
+
+def gs_pass(g, ctx, A, val0, b, b0, s, reps=10):
+    """GS(p) alone on the benchmark system, p = 2, 1 and inf: the device time
+    of the fused one-pass kernel from CUDA events around its launch on the
+    bench stream (gsk_profile_gs_scale; A and b restored before each call,
+    which also pushes most of the 275 MB the kernel moves out of L2), and the
+    whole gs_scale call (clearing the error word, the kernel, the read-back
+    that synchronises) timed by events around it.  Algorithmic bytes per
+    call: rowptr, the values and b read once, the values and b written once."""
+    import torch
+
+    hbm = float(_peaks().get("hbm_gbs", 6800.0))
+    st = torch.cuda.current_stream()
+    by = 4 * (s.n + 1) + 16 * s.nnz + 16 * s.n
+    out = {"algorithmic_bytes": by}
+    for name, p in (("p2", 2.0), ("p1", 1.0), ("p_inf", math.inf)):
+        kern, call = [], []
+        for i in range(3 + reps):
+            A.val.copy_(val0)
+            b.copy_(b0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ms = g.profile_gs_scale(A, b, p=p, ctx=ctx, stream=st)
+            e1.record(st)
+            e1.synchronize()
+            if i >= 3:
+                kern.append(ms / 1e3)
+                call.append(e0.elapsed_time(e1) / 1e3)
+        t = statistics.mean(kern)
+        out[name] = {"us": round(1e6 * t, 2), "GBps": round(by / t / 1e9, 1),
+                     "frac_of_measured_hbm": round(by / t / 1e9 / hbm, 4),
+                     "call_us": round(1e6 * statistics.mean(call), 2)}
+    return out
 
 
 def profile_pass(g, ctx, A, val0, b, b0, s):
@@ -843,16 +947,27 @@ def profile_pass(g, ctx, A, val0, b, b0, s):
 
 
 # ---------------------------------------------------------------- CPU oracle
-def cpu_sample(s, bcg_iters=80, gm_cycles=3):
-    """The CPU oracle (one thread) on a bounded sample of the workload: GS(2),
-    bcg_iters Bi-CGSTAB iterations and gm_cycles full GMRES(30) cycles (10-15 s
-    of CPU work), scaled to a whole solve by the oracle's own iteration
-    counts for this workload (tests/golden/c2_oracle_counts.json)."""
+_CPU_SYS = {}
+
+
+def _cpu_init(grid):
+    """Worker set-up: the workload and its GS(2) scaling, once per process."""
     import oracle
 
-    counts = json.load(open(os.path.join(ROOT, "tests", "golden", "c2_oracle_counts.json")))
-    t0 = time.perf_counter()
+    s = workload(grid)
     val, b, _ = oracle.gs_scale(s.rowptr, s.colidx, s.val, s.b, 2.0)
+    _CPU_SYS["s"], _CPU_SYS["val"], _CPU_SYS["b"] = s, val, b
+
+
+def _cpu_task(args):
+    """One bounded oracle sample (one thread): per-iteration and per-cycle
+    seconds of Bi-CGSTAB and GMRES(30), and GS(2) seconds."""
+    import oracle
+
+    bcg_iters, gm_cycles = args
+    s, val, b = _CPU_SYS["s"], _CPU_SYS["val"], _CPU_SYS["b"]
+    t0 = time.perf_counter()
+    oracle.gs_scale(s.rowptr, s.colidx, s.val, s.b, 2.0)
     t_gs = time.perf_counter() - t0
     t0 = time.perf_counter()
     oracle.bicgstab(s.rowptr, s.colidx, val, b, tol=TOL, maxit=bcg_iters)
@@ -860,13 +975,78 @@ def cpu_sample(s, bcg_iters=80, gm_cycles=3):
     t0 = time.perf_counter()
     oracle.gmres(s.rowptr, s.colidx, val, b, m=M_GMRES, tol=TOL, maxit=M_GMRES * gm_cycles)
     t_cyc = (time.perf_counter() - t0) / gm_cycles
-    nb = counts["bicgstab"]["iters"]
-    ng = counts["gmres30"]["iters"]
-    t_step = t_gs + t_b * nb + t_cyc * math.ceil(ng / M_GMRES)
-    return {"value": SOLVES_PER_STEP / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"GS(2) + {bcg_iters} Bi-CGSTAB iterations + {gm_cycles} GMRES(30) cycles on the 128^3 "
-                      f"workload, scaled to {nb} Bi-CGSTAB iterations and {ng} GMRES steps (the oracle's own counts)",
-            "sample_seconds": round(t_gs + t_b * bcg_iters + t_cyc * gm_cycles, 2)}
+    return t_gs, t_b, t_cyc
+
+
+def _cpu_step_seconds(t_gs, t_b, t_cyc):
+    """Seconds of one step (GS(2) + both solves) from a sample, scaled by the
+    oracle's own iteration counts for this workload."""
+    counts = json.load(open(os.path.join(ROOT, "tests", "golden", "c2_oracle_counts.json")))
+    nb, ng = counts["bicgstab"]["iters"], counts["gmres30"]["iters"]
+    return t_gs + t_b * nb + t_cyc * math.ceil(ng / M_GMRES), nb, ng
+
+
+class CpuOracle:
+    """The plain single-threaded oracle on the host: one process alone (one
+    core), and one process per core of the affinity mask at once (the host's
+    throughput: independent solves, the oracle itself unthreaded; at most
+    MAX_PROCS processes, about 1 GB each at 128^3).  Processes are spawned
+    (never forked after CUDA has started); every wait on them is bounded."""
+
+    MAX_PROCS = 32
+    TIMEOUT_S = 600
+
+    def __init__(self, grid):
+        import multiprocessing as mp
+
+        self.cores = min(len(os.sched_getaffinity(0)), self.MAX_PROCS)
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_cpu_init, initargs=(grid,))
+        # every worker builds its workload before the first timed sample
+        self.pool.map_async(_cpu_task, [(1, 1)] * self.cores, chunksize=1).get(self.TIMEOUT_S)
+
+    def one_core(self, bcg_iters, gm_cycles):
+        return self.pool.apply_async(_cpu_task, ((bcg_iters, gm_cycles),)).get(self.TIMEOUT_S)
+
+    def all_cores(self, bcg_iters, gm_cycles):
+        return self.pool.map_async(_cpu_task, [(bcg_iters, gm_cycles)] * self.cores,
+                                   chunksize=1).get(self.TIMEOUT_S)
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+
+def cpu_sample(grid, bcg_iters=80, gm_cycles=3, all_bcg_iters=40, all_gm_cycles=1):
+    """The CPU oracle on a bounded sample of the workload: GS(2), bcg_iters
+    Bi-CGSTAB iterations and gm_cycles full GMRES(30) cycles on one core
+    (about 20 s), scaled to whole solves by the oracle's own iteration counts
+    (tests/golden/c2_oracle_counts.json); then a shorter sample on every core
+    of the affinity mask at once (one independent sample per core), which is
+    the reported value."""
+    import platform
+
+    cpu = CpuOracle(grid)
+    try:
+        t1, nb, ng = _cpu_step_seconds(*cpu.one_core(bcg_iters, gm_cycles))
+        t_all = [_cpu_step_seconds(*r)[0] for r in cpu.all_cores(all_bcg_iters, all_gm_cycles)]
+    finally:
+        cpu.close()
+    all_rate = sum(SOLVES_PER_STEP / t for t in t_all)
+    model = platform.processor() or platform.machine()
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"value": all_rate, "unit": UNIT, "cores": cpu.cores, "kind": "oracle", "cpu": model,
+            "sample": f"GS(2) + {all_bcg_iters} Bi-CGSTAB iterations + {all_gm_cycles} GMRES(30) cycle(s) on "
+                      f"the 128^3 workload in each of {cpu.cores} single-threaded oracle processes at once, "
+                      f"scaled to {nb} Bi-CGSTAB iterations and {ng} GMRES steps (the oracle's own counts)",
+            "one_core": {"value": SOLVES_PER_STEP / t1, "unit": UNIT, "cores": 1,
+                         "sample": f"GS(2) + {bcg_iters} Bi-CGSTAB iterations + {gm_cycles} GMRES(30) cycles, "
+                                   f"one process alone"}}
 
 
 def run_reference(args):
@@ -874,27 +1054,36 @@ def run_reference(args):
     if rank != 0:
         return
     s = workload(args.grid)
+    cpu = CpuOracle(args.grid)
     samples = []
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        c = cpu_sample(s, bcg_iters=10, gm_cycles=1)
-        if i >= args.warmup:
-            samples.append((c, time.perf_counter() - t0))
-    val = statistics.mean(c["value"] for c, _ in samples)
-    c0 = samples[0][0]
+    try:
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            res = cpu.all_cores(10, 1)
+            if i >= args.warmup:
+                rate = sum(SOLVES_PER_STEP / _cpu_step_seconds(*r)[0] for r in res)
+                samples.append((rate, time.perf_counter() - t0))
+    finally:
+        cpu.close()
+    val = statistics.mean(r for r, _ in samples)
+    sample = (f"per step: GS(2) + 10 Bi-CGSTAB iterations + 1 GMRES(30) cycle on the 128^3 workload in each of "
+              f"{cpu.cores} single-threaded oracle processes at once, scaled to whole solves by the oracle's "
+              f"own iteration counts")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.mean(t for _, t in samples), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
             "config": config_dict(s, world),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": c0["sample"]},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu.cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def profile_kernels(args):
     """Kernel-only run for ncu: GS(2) on the workload, then the FP64 solvers'
-    kernels driven from a host loop for a fixed number of iterations."""
+    kernels driven from a host loop for a fixed number of iterations; with
+    "gs", GS(p) alone --gs-calls times on the pristine workload, for each p of
+    --gs-p (the matrix restored between calls)."""
     import torch
 
     import paper_0812_2769_gb300 as g
@@ -902,6 +1091,15 @@ def profile_kernels(args):
     s = workload(args.grid)
     A = g.Csr.from_host(s.rowptr, s.colidx, s.val)
     b = torch.as_tensor(s.b, device="cuda")
+    if args.profile_kernels == "gs":
+        val0, b0 = A.val.clone(), b.clone()
+        for p in args.gs_p:
+            for _ in range(args.gs_calls):
+                A.val.copy_(val0)
+                b.copy_(b0)
+                ms = g.profile_gs_scale(A, b, p=p)
+                print(f"gs p={p:g} kernel {1e3 * ms:.1f} us")
+        return
     g.gs_scale(A, b, p=2.0)
     for solver, iters in (("gmres", args.gmres_iters), ("bicgstab", args.bicgstab_iters)):
         if args.profile_kernels in (solver, "both"):

@@ -18,7 +18,8 @@
  *  - No C++ exception crosses the ABI.  Every call returns a gsk_status; the
  *    text of the last error of a context is available from gsk_last_error.
  *  - Non-convergence is not an error: a solve returns GSK_OK with
- *    info->conv != GSK_CONVERGED (the paper's "no conv.", Sec. 2.2).
+ *    info->conv != GSK_CONVERGED (a run that misses the goal within maxit,
+ *    which the paper's tables mark as not converged, Sec. 2.2).
  *  - One context runs one solve at a time: calls that share a context must be
  *    issued on the same stream (or be serialised by the caller).  Use one
  *    context per concurrent stream.
@@ -397,6 +398,16 @@ const char* gsk_kernel_name(int kernel);
 gsk_status gsk_profile_solve(gsk_ctx* ctx, int solver, const gsk_csr* A, const void* b, void* x, int m,
                              double tol, const gsk_opts* opts, int max_iters, gsk_launch_record* recs, int cap,
                              int* nrec, gsk_info* info, void* stream);
+
+/*
+ * gsk_profile_gs_scale -- gs_scale (same arguments, same kernel, same
+ * results and errors), and the device time of the GS(p) kernel alone in
+ * *kernel_ms (host), from a CUDA event pair around its launch on `stream`.
+ * A profiling aid: gs_scale's own time also holds the clearing of the error
+ * word and the read-back that synchronises the stream.
+ */
+gsk_status gsk_profile_gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, void* stream,
+                                float* kernel_ms);
 
 /* Device workspace a solve of this shape needs (solver: 0 = GMRES, 1 =
  * Bi-CGSTAB), so that callers can budget HBM before admitting work. */

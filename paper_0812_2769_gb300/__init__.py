@@ -78,6 +78,8 @@ SIGNATURES = {
     "gsk_last_error": ([C.c_void_p], C.c_char_p),
     "gsk_opts_default": ([C.POINTER(OptsC)], None),
     "gs_scale": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p], C.c_int),
+    "gsk_profile_gs_scale": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
+                              C.POINTER(C.c_float)], C.c_int),
     "gs_scale_static": ([C.POINTER(CsrC), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p], C.c_int),
     "gs_scale_sym": ([C.c_void_p, C.POINTER(CsrC), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p],
                      C.c_int),
@@ -450,6 +452,17 @@ def profile_solve(A: Csr, b, x, solver: str = "bicgstab", m: int = 30, tol: floa
                                       C.byref(info), _stream_ptr(stream)))
     out = [(lib().gsk_kernel_name(r.kernel).decode(), r.step, r.ms) for r in recs[: nrec.value]]
     return out, info.as_dict()
+
+
+def profile_gs_scale(A: Csr, b=None, p: float = 2.0, d_out=None, ctx: Context | None = None, stream=None) -> float:
+    """gs_scale, returning the device time of its GS(p) kernel alone in ms
+    (CUDA events around the launch; a profiling aid)."""
+    ctx = ctx or default_context(A.val.device.index or 0)
+    Ac = A.c()
+    ms = C.c_float()
+    ctx.check(lib().gsk_profile_gs_scale(ctx.handle, C.byref(Ac), _ptr(b), float(p), _ptr(d_out),
+                                         _stream_ptr(stream), C.byref(ms)))
+    return ms.value
 
 
 def small_system_rows(ctx: Context | None = None) -> int:

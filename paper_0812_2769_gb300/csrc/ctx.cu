@@ -128,6 +128,18 @@ gsk_status gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, 
   return gsk::run_gs_scale(ctx, A, b, p, d_out, (cudaStream_t)stream);
 }
 
+gsk_status gsk_profile_gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, void* stream,
+                                float* kernel_ms) {
+  if (!ctx) return GSK_ERR_ARG;
+  if (!kernel_ms) return ctx->fail(GSK_ERR_ARG, "NULL kernel_ms");
+  *kernel_ms = 0.0f;
+  gsk_status s = gsk::check_csr(ctx, A);
+  if (s != GSK_OK) return s;
+  if (!(p >= 1.0)) return ctx->fail(GSK_ERR_ARG, "p must be >= 1 or INFINITY");
+  if (A->n == 0) return GSK_OK;
+  return gsk::run_gs_scale(ctx, A, b, p, d_out, (cudaStream_t)stream, kernel_ms);
+}
+
 gsk_status gs_scale_sym(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* s_out, double* w_out, void* stream) {
   if (!ctx) return GSK_ERR_ARG;
   gsk_status s = gsk::check_csr(ctx, A);

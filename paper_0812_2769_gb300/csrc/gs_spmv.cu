@@ -204,7 +204,8 @@ gsk_status launch_spmv(gsk_ctx* ctx, const gsk_csr* A, const void* x, void* y, i
   return GSK_OK;
 }
 
-gsk_status run_gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, cudaStream_t st) {
+gsk_status run_gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, cudaStream_t st,
+                        float* kernel_ms) {
   const int n = A->n;
   Arena a;
   a.take<int>(64);  // error word
@@ -212,14 +213,26 @@ gsk_status run_gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_o
   if (s != GSK_OK) return s;
   int* err = (int*)ctx->ws;
   GSK_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (kernel_ms) {
+    GSK_CK(cudaEventCreate(&ev[0]));
+    GSK_CK(cudaEventCreate(&ev[1]));
+    GSK_CK(cudaEventRecord(ev[0], st));
+  }
   if (A->dtype == GSK_F64)
     launch_gs_rows<double, true>(ctx, 0, n, A->nnz, A->rowptr, (double*)A->val, (double*)b, p, d_out, err, st);
   else
     launch_gs_rows<float, true>(ctx, 0, n, A->nnz, A->rowptr, (float*)A->val, (float*)b, p, d_out, err, st);
   GSK_CK(cudaGetLastError());
+  if (kernel_ms) GSK_CK(cudaEventRecord(ev[1], st));
   int* hbits = (int*)ctx->host_pinned;
   GSK_CK(cudaMemcpyAsync(hbits, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   GSK_CK(cudaStreamSynchronize(st));
+  if (kernel_ms) {
+    GSK_CK(cudaEventElapsedTime(kernel_ms, ev[0], ev[1]));
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+  }
   return err_bits_status(ctx, *hbits);
 }
 

@@ -211,7 +211,10 @@ gsk_status launch_spmv(gsk_ctx* ctx, const gsk_csr* A, const void* x, void* y, i
 void launch_gs_norm(gsk_ctx* ctx, int n, int nnz, const int* rowptr, const double* val, double p, double* d,
                     int* err, cudaStream_t st);
 void launch_unit_check(gsk_ctx* ctx, int n, const double* w, const GridRed& red, int* out, cudaStream_t st);
-gsk_status run_gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, cudaStream_t st);
+// kernel_ms (host, optional): device time of the GS(p) kernel alone, from a
+// CUDA event pair around its launch.
+gsk_status run_gs_scale(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* d_out, cudaStream_t st,
+                        float* kernel_ms = nullptr);
 gsk_status run_gs_scale_sym(gsk_ctx* ctx, gsk_csr* A, void* b, double p, double* s_out, double* w_out,
                             cudaStream_t st);
 gsk_status launch_diag_mul(gsk_ctx* ctx, int n, const double* s, void* x, gsk_dtype dtype, cudaStream_t st);

@@ -50,7 +50,7 @@ def test_recorded_traffic_follows_the_source_hash(monkeypatch):
     if got is None:
         pytest.skip("profiles/dram_traffic.txt was taken on other kernel sources")
     assert 2.5e8 < got < 3.5e8  # one pass over 16-17 basis columns of 2.1 M rows
-    monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)
+    monkeypatch.setattr(bench, "source_hash", lambda files=None: "0" * 16)
     assert bench.recorded_traffic("gm_gb_cgs_pass2") is None
 
 
@@ -62,3 +62,20 @@ def test_source_hash_covers_the_measured_kernels():
         assert os.path.exists(os.path.join(d, fn)), fn
     for fn in ("gmres_kernels.cuh", "bicgstab_kernels.cuh", "spmv_tma.cuh", "device_common.cuh"):
         assert fn in bench.TRAFFIC_SOURCES
+    for fn in bench.GS_SOURCES:
+        assert os.path.exists(os.path.join(d, fn)), fn
+    assert "gs_spmv.cu" in bench.GS_SOURCES and "device_common.cuh" in bench.GS_SOURCES
+
+
+def test_cpu_baseline_on_one_core_and_on_every_core():
+    # the oracle in spawned single-threaded processes, on a small grid: one
+    # process alone, then one per core of the affinity mask at once
+    import os
+
+    out = bench.cpu_sample(10, bcg_iters=2, gm_cycles=1, all_bcg_iters=2, all_gm_cycles=1)
+    assert out["kind"] == "oracle" and out["unit"] == bench.UNIT
+    assert out["cores"] == min(len(os.sched_getaffinity(0)), bench.CpuOracle.MAX_PROCS)
+    assert out["value"] > 0 and out["one_core"]["value"] > 0 and out["one_core"]["cores"] == 1
+    # independent processes: all cores together beat one alone
+    if out["cores"] > 1:
+        assert out["value"] > out["one_core"]["value"]

@@ -133,6 +133,29 @@ def test_gs_bad_p_rejected():
         g.gs_scale(A, b, p=0.5)
 
 
+def test_profiled_gs_scale_is_gs_scale():
+    # the profiling entry runs the same kernel: bitwise the same results, and
+    # the kernel's own device time
+    import torch
+
+    g = gsk()
+    s = configs.c2(21)
+    A1, b1 = to_dev(g, s)
+    A2, b2 = to_dev(g, s)
+    d1 = torch.empty(s.n, dtype=torch.float64, device="cuda")
+    d2 = torch.empty_like(d1)
+    g.gs_scale(A1, b1, p=2.0, d_out=d1)
+    ms = g.profile_gs_scale(A2, b2, p=2.0, d_out=d2)
+    assert ms > 0.0
+    assert torch.equal(A1.val, A2.val) and torch.equal(b1, b2) and torch.equal(d1, d2)
+    val = s.val.copy()
+    val[s.rowptr[5]:s.rowptr[6]] = 0.0
+    A3, b3 = to_dev(g, cd.System(s.n, s.rowptr, s.colidx, val, s.b))
+    with pytest.raises(g.GskError) as ei:
+        g.profile_gs_scale(A3, b3, p=2.0)
+    assert ei.value.status == g.ERR_ZERO_ROW
+
+
 # ------------------------------------------------------------------ SpMV
 def _spmv_case(sys_, x):
     import torch
