@@ -775,6 +775,25 @@ def batched_pass(g, args):
                      "converged": sum(i["conv"] == g.CONVERGED for i in infos),
                      "iters_mean": float(sum(i["iters"] for i in infos) / len(infos)),
                      "autotuned": cfg, "tuning_seconds": round(t_tune, 2), "default_shape_ms": default_ms}
+    # per-iteration cost of the two arithmetic forms, from two fixed
+    # iteration counts (tol 0: a system runs to maxit unless it breaks down):
+    # FP64 Bi-CGSTAB iterations, and the FP32 iterations of the mixed form
+    # (one inner solve of maxit iterations, inner_tol 1e-300); the slope
+    # between the two counts leaves out GS, the FP32 copy of the matrix and
+    # the residuals
+    per = {}
+    for name, prec in (("f64", g.PREC_F64), ("f32_inner", g.PREC_MIXED)):
+        pts = []
+        for M in (20, 60):
+            reset()
+            o = g.opts(precision=prec, maxit=M, inner_maxit=M, inner_tol=1e-300)
+            infos, _ = g.bicgstab_solve_batched(As, bs, xs, p=2.0, tol=0.0, options=o, ctx=ctx)
+            pts.append((sum(i["iters"] for i in infos), infos[0]["ms"]))
+        (i1, t1), (i2, t2) = pts
+        per[name] = {"ns_per_system_iteration": round(1e6 * (t2 - t1) / max(i2 - i1, 1), 3),
+                     "system_iterations": [i1, i2], "ms": [round(t1, 3), round(t2, 3)]}
+    per["f32_over_f64"] = round(per["f32_inner"]["ns_per_system_iteration"] / per["f64"]["ns_per_system_iteration"], 3)
+    out["per_iteration"] = per
     # batched GMRES(30), FP64, on the first 1024 systems (restarted GMRES
     # stagnates on many of these inclusion systems: capped at 1000 steps)
     K = min(1024, len(systems))
@@ -1040,6 +1059,8 @@ def cpu_sample(grid, bcg_iters=80, gm_cycles=3, all_bcg_iters=40, all_gm_cycles=
                 break
     except OSError:
         pass
+    # Arm reports a part number: name the ones of this family
+    model = {"0xd4f": "Arm Neoverse V2 (cpu part 0xd4f)", "0xd8e": "Arm Neoverse V3 (cpu part 0xd8e)"}.get(model, model)
     return {"value": all_rate, "unit": UNIT, "cores": cpu.cores, "kind": "oracle", "cpu": model,
             "sample": f"GS(2) + {all_bcg_iters} Bi-CGSTAB iterations + {all_gm_cycles} GMRES(30) cycle(s) on "
                       f"the 128^3 workload in each of {cpu.cores} single-threaded oracle processes at once, "
