@@ -358,14 +358,19 @@ def run_gpu(args):
         other_line = {"value": sum_over_ranks(dist, SOLVES_PER_STEP * args.steps) / t_other, "unit": UNIT,
                       "ms_per_step": t_other * 1e3 / args.steps}
 
-    # kernels launched in the timed region (per step: 2 for GS(2); each solve
-    # from its counters -- see the launch structure of the two graphs)
+    # kernels launched in the timed region, from each solve's counters and
+    # the launch structure of its graph (kernels that return at entry count):
+    # GS(2) one kernel; Bi-CGSTAB: weights, unit check and init, then a WHILE
+    # body of 4 iterations x 5 kernels + kt + kr per pass, ceil(iters / 4)
+    # passes between confirmations and one more per refresh; GMRES(30):
+    # weights, unit check and init, then per cycle the 30 unrolled steps (4
+    # kernels each: the product and the three CGS passes) and gy, gx, gr
+    per_step = 4
     launches = 0
     for i1, i2 in infos:
-        checks = i1["refreshes"] + 1
-        launches += 2
-        launches += 3 + 4 * i1["iters"] + (i1["iters"] - checks) + 2 * checks
-        launches += 3 + 4 * i2["iters"] + 3 * (i2["restarts"] + 1)
+        launches += 1
+        launches += 3 + 22 * (math.ceil(i1["iters"] / 4) + i1["refreshes"])
+        launches += 3 + (i2["restarts"] + 1) * (M_GMRES * per_step + 3)
     ok = all(i1["conv"] == g.CONVERGED and i2["conv"] == g.CONVERGED and i1["relres_true"] < TOL
              and i2["relres_true"] < TOL for i1, i2 in infos)
 

@@ -348,9 +348,12 @@ gsk_status gsk_small_system_rows(gsk_ctx* ctx, int* rows);
  *           refinement step gains less than 10x in the FP64 metric is
  *           finished by FP64 Bi-CGSTAB from its current x;
  *           batch_block (threads per block: 128, 256, 512; 0 = 256) and
- *           batch_large_n (systems with more rows are solved first, one at
- *           a time, by gs_scale and the grid-wide solver with the same
- *           options; 0 = none) shape the launch
+ *           batch_large_n (systems with more rows are solved one at a
+ *           time by gs_scale and the grid-wide solver with the same
+ *           options, beside the persistent launch: on a second stream with
+ *           a child context of ctx, which keeps its own workspace; `stream`
+ *           waits for them before the call returns; 0 = none) shape the
+ *           launch
  *   infos   host array [nsys] or NULL; status host array [nsys] or NULL
  *           (per-system gsk_status: GSK_ERR_ZERO_ROW / NONFINITE / ARG).
  * When infos or status is given the call synchronises `stream`; it returns

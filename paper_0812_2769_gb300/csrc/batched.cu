@@ -727,10 +727,32 @@ static int batch_blocks_per_sm(int solver, bool mixed) {
   return (e != cudaSuccess || per_sm < 1) ? 1 : per_sm;
 }
 
+// The grid-wide lane of a batch: the context's child context and stream,
+// created on first use.
+static gsk_status batch_aux(gsk_ctx* ctx) {
+  if (ctx->aux) return GSK_OK;
+  gsk_ctx* aux = nullptr;
+  gsk_status s = gsk_ctx_create(&aux, ctx->device);
+  if (s != GSK_OK) return ctx->fail(s, "creating the batch's grid-wide lane failed");
+  cudaError_t e = cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    gsk_ctx_destroy(aux);
+    return ctx->cuda_fail(e, "creating the batch's grid-wide lane");
+  }
+  ctx->aux = aux;
+  return GSK_OK;
+}
+
 // solver 0: GMRES(m[i]) (FP64), 1: Bi-CGSTAB (FP64 or mixed).  Systems with
-// more than opts.batch_large_n rows are solved first, one at a time, by the
-// grid-wide solvers (gs_scale, then gmres_solve / bicgstab_solve with the
-// same options); the others by one persistent launch, one block each.
+// more than opts.batch_large_n rows go to the grid-wide solvers (gs_scale,
+// then gmres_solve / bicgstab_solve with the same options), one at a time;
+// the others to one persistent launch, one block each.  When a batch has
+// both, the persistent launch goes first on `stream` and the grid-wide
+// solves run beside it on a second stream with a child context (its own
+// workspace), their kernels taking the SMs the batch's blocks leave as
+// they finish; `stream` waits for both before the call returns.
 static gsk_status batch_solve(gsk_ctx* ctx, int solver, int nsys, const gsk_csr* A, void* const* b, void* const* x,
                               const double* p, const int* mvec, double tol, const gsk_opts* opts_in, gsk_info* infos,
                               int32_t* status, void* stream) {
@@ -773,19 +795,35 @@ static gsk_status batch_solve(gsk_ctx* ctx, int solver, int nsys, const gsk_csr*
   if (solver == 0 && mixed && !small.empty())
     return ctx->fail(GSK_ERR_ARG, "the one-block GMRES is FP64: mixed precision only with batch_large_n routing");
   gsk_status worst = GSK_OK;
+  std::string first_error;
   cudaStream_t st = (cudaStream_t)stream;
-  // large systems: the grid-wide path, one after the other
-  for (int i : large) {
-    gsk_info inf = {};
-    gsk_status si = GSK_OK;
-    if (!(hs[i].p != hs[i].p)) si = gs_scale(ctx, const_cast<gsk_csr*>(&A[i]), b[i], hs[i].p, nullptr, stream);
-    if (si == GSK_OK)
-      si = solver == 0 ? gmres_solve(ctx, &A[i], b[i], x[i], mvec[i], tol, &opts, &inf, stream)
-                       : bicgstab_solve(ctx, &A[i], b[i], x[i], tol, &opts, &inf, stream);
-    if (infos) infos[i] = inf;
-    if (status) status[i] = si;
-    if (si != GSK_OK && worst == GSK_OK) worst = si;
+  // grid-wide lane: beside the persistent launch when there is one
+  const bool beside = !large.empty() && !small.empty();
+  gsk_ctx* lctx = ctx;
+  cudaStream_t lst = st;
+  if (beside) {
+    gsk_status s = batch_aux(ctx);
+    if (s != GSK_OK) return s;
+    lctx = ctx->aux;
+    lst = ctx->aux_stream;
+    // size the lane's workspace for its largest system now: growing it later
+    // would free memory, which waits for the whole device
+    size_t need = 0;
+    for (int i : large) {
+      size_t bi = 0;
+      if (gsk_workspace_bytes(A[i].n, A[i].nnz, solver == 0 ? 0 : 1, solver == 0 ? mvec[i] : 1, opts.precision,
+                              &bi) == GSK_OK)
+        need = std::max(need, bi);
+    }
+    if ((s = lctx->reserve(need)) != GSK_OK) {
+      ctx->last_error = lctx->last_error;
+      return s;
+    }
+    // the second stream starts after the work the caller queued on `stream`
+    GSK_CK(cudaEventRecord(ctx->ev_fork, st));
+    GSK_CK(cudaStreamWaitEvent(lst, ctx->ev_fork, 0));
   }
+  BatchOut* dout = nullptr;
   if (!small.empty()) {
     const int ns = (int)small.size();
     // largest systems first
@@ -808,7 +846,7 @@ static gsk_status batch_solve(gsk_ctx* ctx, int solver, int nsys, const gsk_csr*
     BatchSys* dsys = ar.take<BatchSys>(nsys);
     int* dorder = ar.take<int>(ns);
     int* dm = ar.take<int>(nsys);
-    BatchOut* dout = ar.take<BatchOut>(nsys);
+    dout = ar.take<BatchOut>(nsys);
     char* scratch = ar.take<char>(slot * grid);
     GSK_CK(cudaEventRecord(ctx->ev0, st));
     GSK_CK(cudaMemsetAsync(queue, 0, sizeof(unsigned), st));
@@ -823,21 +861,43 @@ static gsk_status batch_solve(gsk_ctx* ctx, int solver, int nsys, const gsk_csr*
     else batch_launch<512>(solver, mixed, grid, P, st);
     GSK_CK(cudaGetLastError());
     GSK_CK(cudaEventRecord(ctx->ev1, st));
-    if (infos || status) {
-      std::vector<BatchOut> ho(nsys);
-      GSK_CK(cudaMemcpyAsync(ho.data(), dout, sizeof(BatchOut) * nsys, cudaMemcpyDeviceToHost, st));
-      GSK_CK(cudaStreamSynchronize(st));
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-      for (int i : small) {
-        if (infos) infos[i] = gsk_info{ho[i].iters, ho[i].restarts, ho[i].refreshes, ho[i].refinements, ho[i].conv,
-                                       ho[i].relres_true, ho[i].relres_rec, ms};
-        if (status) status[i] = ho[i].status;
-        if (ho[i].status != GSK_OK && worst == GSK_OK) worst = (gsk_status)ho[i].status;
-      }
+  }
+  // large systems: the grid-wide path, one after the other (each call waits
+  // for its own stream only, so the persistent launch keeps running)
+  for (int i : large) {
+    gsk_info inf = {};
+    gsk_status si = GSK_OK;
+    if (!(hs[i].p != hs[i].p)) si = gs_scale(lctx, const_cast<gsk_csr*>(&A[i]), b[i], hs[i].p, nullptr, lst);
+    if (si == GSK_OK)
+      si = solver == 0 ? gmres_solve(lctx, &A[i], b[i], x[i], mvec[i], tol, &opts, &inf, lst)
+                       : bicgstab_solve(lctx, &A[i], b[i], x[i], tol, &opts, &inf, lst);
+    if (infos) infos[i] = inf;
+    if (status) status[i] = si;
+    if (si != GSK_OK && worst == GSK_OK) {
+      worst = si;
+      first_error = lctx->last_error;
     }
   }
-  if (worst != GSK_OK) return ctx->fail(worst, "at least one system of the batch failed (see status[])");
+  if (beside) {
+    GSK_CK(cudaEventRecord(ctx->ev_join, lst));
+    GSK_CK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+  }
+  if (dout && (infos || status)) {
+    std::vector<BatchOut> ho(nsys);
+    GSK_CK(cudaMemcpyAsync(ho.data(), dout, sizeof(BatchOut) * nsys, cudaMemcpyDeviceToHost, st));
+    GSK_CK(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    for (int i : small) {
+      if (infos) infos[i] = gsk_info{ho[i].iters, ho[i].restarts, ho[i].refreshes, ho[i].refinements, ho[i].conv,
+                                     ho[i].relres_true, ho[i].relres_rec, ms};
+      if (status) status[i] = ho[i].status;
+      if (ho[i].status != GSK_OK && worst == GSK_OK) worst = (gsk_status)ho[i].status;
+    }
+  }
+  if (worst != GSK_OK)
+    return ctx->fail(worst, "at least one system of the batch failed (see status[])" +
+                                (first_error.empty() ? std::string() : ": " + first_error));
   return GSK_OK;
 }
 

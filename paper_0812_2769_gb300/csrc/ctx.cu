@@ -95,6 +95,11 @@ gsk_status gsk_ctx_destroy(gsk_ctx* ctx) {
   if (!ctx) return GSK_OK;
   cudaSetDevice(ctx->device);
   ctx->clear_graphs();
+  if (ctx->aux) gsk_ctx_destroy(ctx->aux);
+  cudaSetDevice(ctx->device);
+  if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
   if (ctx->capture) cudaStreamDestroy(ctx->capture);

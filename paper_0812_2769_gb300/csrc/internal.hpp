@@ -65,6 +65,12 @@ struct gsk_ctx {
   // pinned host staging for small read-backs
   void* host_pinned = nullptr;
   cudaStream_t capture = nullptr;  // private stream used only for graph capture
+  // the batched solvers' grid-wide lane: a child context (its own workspace
+  // and graphs) and stream, so that systems routed out of a batch run beside
+  // its persistent launch; created on first use
+  gsk_ctx* aux = nullptr;
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<gsk::GraphEntry> graphs;
   uint64_t clock = 0;

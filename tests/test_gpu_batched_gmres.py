@@ -140,6 +140,49 @@ def test_large_systems_take_the_grid_wide_solver(solver):
     assert big > thr
 
 
+def test_routed_systems_run_beside_the_batch():
+    """The systems above batch_large_n run on the grid-wide lane beside the
+    persistent launch (a second stream, a child context): the batch's own
+    systems give bitwise the results of a batch without them, the routed ones
+    those of direct calls, and a failing routed system reports its own
+    status (and its error text) while the others complete."""
+    import torch
+
+    g = gsk()
+    systems = [configs.c4_system(i) for i in range(10)]
+    thr = sorted(s.n for s in systems)[5]
+    As, bs, xs = _upload(g, systems)
+    infos, stat = g.bicgstab_solve_batched(As, bs, xs, p=2.0, tol=1e-8, options=g.opts(batch_large_n=thr))
+    assert all(st == g.OK for st in stat)
+    small = [i for i, s in enumerate(systems) if s.n <= thr]
+    large = [i for i, s in enumerate(systems) if s.n > thr]
+    assert small and large
+    A2, b2, x2 = _upload(g, [systems[i] for i in small])
+    inf2, _ = g.bicgstab_solve_batched(A2, b2, x2, p=2.0, tol=1e-8)
+    for q, i in enumerate(small):
+        assert torch.equal(x2[q], xs[i]) and inf2[q]["iters"] == infos[i]["iters"]
+    for i in large:
+        A1, b1, x1 = _upload(g, [systems[i]])
+        g.gs_scale(A1[0], b1[0], p=2.0)
+        ref = g.bicgstab_solve(A1[0], b1[0], x1[0], tol=1e-8)
+        assert torch.equal(x1[0], xs[i]) and ref["iters"] == infos[i]["iters"]
+    # a routed system with a zero row
+    bad = large[0]
+    s = systems[bad]
+    val = s.val.copy()
+    val[s.rowptr[3]:s.rowptr[4]] = 0.0
+    systems_bad = list(systems)
+    systems_bad[bad] = cd.System(s.n, s.rowptr, s.colidx, val, s.b)
+    As, bs, xs = _upload(g, systems_bad)
+    with pytest.raises(g.GskError) as ei:
+        g.bicgstab_solve_batched(As, bs, xs, p=2.0, tol=1e-8, options=g.opts(batch_large_n=thr))
+    assert ei.value.status == g.ERR_ZERO_ROW
+    infos, stat = g.bicgstab_solve_batched(As, bs, xs, p=2.0, tol=1e-8, options=g.opts(batch_large_n=thr),
+                                           check=False)
+    assert stat[bad] == g.ERR_ZERO_ROW
+    assert all(st == g.OK for i, st in enumerate(stat) if i != bad)
+
+
 def test_batched_gmres_rejects_bad_shapes():
     g = gsk()
     systems = [configs.c4_system(0)]
