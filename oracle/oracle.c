@@ -329,7 +329,10 @@ int or_gmres(int n, const int* rp, const int* ci, const double* va,
              const double* w_in, const double* lu, or_info* info, double* hist,
              double* trace, int trace_cap) {
   memset(info, 0, sizeof(*info));
-  if (n <= 0 || m < 1 || maxit < 0 || !(tol >= 0.0)) return OR_ERR_ARG;
+  if (n < 0 || m < 1 || maxit < 0 || !(tol >= 0.0)) return OR_ERR_ARG;
+  /* the empty system: its residual is the empty vector, of norm 0 -- the
+   * case mu0 = 0 below, converged at x0 without a step */
+  if (n == 0) { info->conv = OR_CONVERGED; return OR_OK; }
   size_t nn = (size_t)n;
   double* V = (double*)malloc(sizeof(double) * nn * (m + 1));
   double* H = (double*)calloc((size_t)(m + 1) * m, sizeof(double));
@@ -465,7 +468,9 @@ int or_bicgstab(int n, const int* rp, const int* ci, const double* va,
                 const double* w_in, const double* lu, or_info* info, double* hist,
                 double* trace, int trace_cap) {
   memset(info, 0, sizeof(*info));
-  if (n <= 0 || maxit < 0 || !(tol >= 0.0) || refresh < 0) return OR_ERR_ARG;
+  if (n < 0 || maxit < 0 || !(tol >= 0.0) || refresh < 0) return OR_ERR_ARG;
+  /* the empty system: converged at x0, as for mu0 = 0 below */
+  if (n == 0) { info->conv = OR_CONVERGED; return OR_OK; }
   size_t nn = (size_t)n;
   double* r = (double*)malloc(sizeof(double) * nn);
   double* rh = (double*)malloc(sizeof(double) * nn);

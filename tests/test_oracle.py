@@ -470,3 +470,21 @@ def test_bicgstab_breakdown_is_reported():
     va = np.array([1.0, -1.0])
     x, info = oracle.bicgstab(rp, ci, va, np.array([1.0, 0.0]), tol=1e-10)
     assert info["conv"] == oracle.BREAKDOWN and info["iters"] == 0
+
+
+def test_the_empty_system_is_solved_at_x0():
+    """n = 0: the residual is the empty vector, of norm 0, so both solvers
+    stop at x0 before any step -- the same outcome as for b = 0 on a
+    non-empty system (Sec. 2.2's test with a zero initial residual)."""
+    rp = np.zeros(1, dtype=np.int32)
+    e = (rp, np.zeros(0, dtype=np.int32), np.zeros(0), np.zeros(0))
+    for x, info in (oracle.bicgstab(*e, tol=1e-8), oracle.gmres(*e, m=10, tol=1e-8)):
+        assert info["conv"] == oracle.CONVERGED and info["iters"] == 0 and info["relres_true"] == 0.0
+        assert len(x) == 0
+    s = configs.c1(6)
+    z = np.zeros(s.n)
+    for x, info in (oracle.bicgstab(s.rowptr, s.colidx, s.val, z, tol=1e-8),
+                    oracle.gmres(s.rowptr, s.colidx, s.val, z, m=10, tol=1e-8)):
+        assert info["conv"] == oracle.CONVERGED and info["iters"] == 0 and not x.any()
+    with pytest.raises(oracle.OracleError):
+        oracle.gmres(rp, e[1], e[2], e[3], m=0, tol=1e-8)
