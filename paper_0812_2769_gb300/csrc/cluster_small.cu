@@ -135,7 +135,9 @@ __global__ void __launch_bounds__(kClusterThreads, 1) bcg_cluster(ClusterBcgArgs
   const int e0 = nloc > 0 ? __ldg(a.rowptr + row0) : 0;
   const int e1 = nloc > 0 ? __ldg(a.rowptr + row0 + nloc) : 0;
   const bool staged = e0 >= 0 && e1 >= e0 && e1 <= a.nnz && e1 - e0 <= a.cap;
-  if (staged) {
+  // (a CTA that owns no row stages nothing: its row0 may lie past rowptr's
+  // last entry)
+  if (staged && nloc > 0) {
     for (int k = threadIdx.x; k < e1 - e0; k += kClusterThreads) {
       const int j = __ldg(a.colidx + e0 + k);
       const int o = (unsigned)j < (unsigned)n ? j / rpc : -1;
