@@ -630,6 +630,13 @@ def c3_pass(g, steps=2000):
                       "frac_of_measured_hbm": round(byt / us / 1e3 / hbm, 3)}
         del xv, yv
     out["spmv"] = spmv
+    # the solvers' kernels on this matrix, from a host loop with CUDA events
+    # around each launch (one GMRES(30) cycle, 10 Bi-CGSTAB iterations): at
+    # 16.8 M rows the fixed per-launch time weighs 8x less than at 128^3
+    A.val.copy_(val0)
+    b.copy_(b0)
+    g.gs_scale(A, b, p=2.0)
+    out["kernels"] = kernel_table(g, A, b, s.n, s.nnz, hbm, (("gmres", 30), ("bicgstab", 10)))
     # what the oracle reaches on the same system (written by
     # tests/golden/make_c3_oracle_trace.py): GMRES(30)'s metric after its first
     # two cycles, and Bi-CGSTAB over a rounding ensemble (none converges to
@@ -645,6 +652,34 @@ def c3_pass(g, steps=2000):
                          "bicgstab_maxit": max(r["iters"] for r in d["bicgstab"])}
     del A, val0, b0, b, x
     torch.cuda.empty_cache()
+    return out
+
+
+def kernel_table(g, A, b, n, nnz, hbm, runs):
+    """Per-kernel averages of gsk_profile_solve launches: us per launch,
+    algorithmic GB/s and FP64 TFLOP/s (kernel_cost), fractions of the HBM
+    and FP64 peaks."""
+    import torch
+
+    agg = {}
+    for solver, iters in runs:
+        x = torch.zeros(n, dtype=torch.float64, device=A.val.device)
+        recs, _ = g.profile_solve(A, b, x, solver=solver, m=M_GMRES, tol=TOL, max_iters=iters)
+        for name, step, ms in recs:
+            by, fl = kernel_cost(name, step, n, nnz)
+            a = agg.setdefault(name, [0, 0.0, 0.0, 0.0])
+            a[0] += 1
+            a[1] += ms
+            a[2] += by
+            a[3] += fl
+        del x
+    out = {}
+    for name, (k, ms, by, fl) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
+        t = ms / 1e3
+        if t <= 0 or by <= 0:
+            continue
+        out[name] = {"launches": k, "us": round(1e6 * t / k, 1), "GBps": round(by / t / 1e9, 1),
+                     "hbm_frac": round(by / t / 1e9 / hbm, 3), "fp64_frac": round(fl / t / 1e12 / FP64_PEAK_TFLOPS, 3)}
     return out
 
 

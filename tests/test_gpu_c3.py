@@ -11,7 +11,7 @@ On this system restarted GMRES(30) stagnates near a relative residual of
 1e-7 (20,000 steps, FP64 and mixed alike) and Bi-CGSTAB does not converge:
 the cell Peclet number reaches ~60 where a = 1e-3, beyond what central
 differences keep well conditioned; 1e-10 is not reached by either method.
-That verdict rests on the oracle (tests/golden/c3_oracle_trace.json, written
+That conclusion rests on the oracle (tests/golden/c3_oracle_trace.json, written
 by the committed script beside it): its GMRES(30) takes the same first 60
 steps (the residual estimate after every step, the true metric after each
 cycle), and its Bi-CGSTAB, on a rounding ensemble of 8 members, runs 3,000
