@@ -279,6 +279,9 @@ gsk_status gsk_spmv(gsk_ctx* ctx, const gsk_csr* A, const void* x, void* y, void
  *   info   host pointer or NULL; when non-NULL the call synchronises `stream`
  *          and fills it.
  * The whole solve runs on the device: no host round trip per iteration.
+ * Small systems (FP64, no preconditioner, at most
+ * gsk_gmres_small_system_rows rows for this m) run on one thread-block
+ * cluster; the decisions are the same, the sums are added in another order.
  */
 gsk_status gmres_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, int m, double tol,
                        const gsk_opts* opts, gsk_info* info, void* stream);
@@ -329,6 +332,18 @@ gsk_status bicgstab_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x
  * for a NULL argument.
  */
 gsk_status gsk_small_system_rows(gsk_ctx* ctx, int* rows);
+
+/*
+ * gsk_gmres_small_system_rows -- the largest system (rows, for matrices of
+ * about 7 nonzeros per row) that gmres_solve with restart length m runs on
+ * one thread-block cluster: 16 CTAs holding the m + 1 basis vectors, x and
+ * the metric weights of their rows in shared memory (so the limit falls as
+ * m grows), the whole solve in one launch.  Whether a given system takes
+ * that path also depends on its nonzeros fitting the CTAs' stages.  0 when
+ * the path is off (GSK_SMALL_N=0) or the device cannot launch the cluster.
+ * m in 1..64; host pointer; GSK_ERR_ARG otherwise.
+ */
+gsk_status gsk_gmres_small_system_rows(gsk_ctx* ctx, int m, int* rows);
 
 /*
  * bicgstab_solve_batched -- GS(p) then Bi-CGSTAB (Sec. 2) on nsys independent

@@ -97,6 +97,7 @@ SIGNATURES = {
                         C.POINTER(OptsC), C.POINTER(InfoC), C.c_void_p], C.c_int),
     "gsk_workspace_bytes": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)], C.c_int),
     "gsk_small_system_rows": ([C.c_void_p, C.POINTER(C.c_int)], C.c_int),
+    "gsk_gmres_small_system_rows": ([C.c_void_p, C.c_int, C.POINTER(C.c_int)], C.c_int),
     "gsk_kernel_name": ([C.c_int], C.c_char_p),
     "bicgstab_solve_batched": ([C.c_void_p, C.c_int, C.POINTER(CsrC), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                 C.POINTER(C.c_double), C.c_double, C.POINTER(OptsC), C.POINTER(InfoC),
@@ -463,6 +464,15 @@ def profile_gs_scale(A: Csr, b=None, p: float = 2.0, d_out=None, ctx: Context | 
     ctx.check(lib().gsk_profile_gs_scale(ctx.handle, C.byref(Ac), _ptr(b), float(p), _ptr(d_out),
                                          _stream_ptr(stream), C.byref(ms)))
     return ms.value
+
+
+def gmres_small_system_rows(m: int = 30, ctx: Context | None = None) -> int:
+    """The largest system (about 7 nonzeros per row) gmres_solve with restart
+    length m runs on one thread-block cluster (0: the path is off)."""
+    ctx = ctx or default_context(0)
+    out = C.c_int()
+    ctx.check(lib().gsk_gmres_small_system_rows(ctx.handle, int(m), C.byref(out)))
+    return out.value
 
 
 def small_system_rows(ctx: Context | None = None) -> int:

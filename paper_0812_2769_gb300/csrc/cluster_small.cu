@@ -24,19 +24,13 @@
 // true-residual confirmation with refreshes, maxit, the metric weights) are
 // those of the grid-wide solver (bicgstab_kernels.cuh); only the order of the
 // additions inside the dot products differs.
-#include <cooperative_groups.h>
-
 #include <algorithm>
 #include <cfloat>
 
-#include "internal.hpp"
-
-namespace cg = cooperative_groups;
+#include "cluster.cuh"
 
 namespace gsk {
 
-constexpr int kClusterCtas = 16;    // CTAs per cluster (a non-portable size)
-constexpr int kClusterThreads = 512;
 constexpr int kClusterVecs = 8;     // x, r, r^, p, v, s, t, W in shared memory
 
 struct ClusterBcgArgs {
@@ -54,56 +48,6 @@ struct ClusterBcgArgs {
   gsk_info* out;        // device: the outcome
   int* err;             // device: kErr* bits
 };
-
-// Sum over the CTA's threads of NV values, then over the cluster's CTAs in
-// rank order.  red: this CTA's two publication buffers (alternating by
-// `round`, so that a CTA may publish the next sums while another still reads
-// the previous ones); wsum: per-warp scratch.  Returns the totals in tot
-// (shared; valid in every thread of every CTA after the call).
-// Only the first `nw` warps hold rows (the others' values are zero and are
-// left out: on this part an FP64 addition costs its pipe time whatever its
-// operands).
-template <int NV>
-__device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, const double (&v)[NV], double* red,
-                                            double* wsum, double* tot, int& round, int nw) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (wid < nw) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      const double s = warp_allsum(v[k]);
-      if (lane == 0) wsum[wid * NV + k] = s;
-    }
-  }
-  __syncthreads();
-  double* mine = red + (round & 1) * 8;
-  if (threadIdx.x < NV) {
-    // the warps' sums in a fixed pairwise tree (a serial chain of FP64
-    // additions costs a full pipe pass per addition on this part)
-    double q[kClusterThreads / 32];
-#pragma unroll
-    for (int w = 0; w < kClusterThreads / 32; ++w) q[w] = w < nw ? wsum[w * NV + threadIdx.x] : 0.0;
-#pragma unroll
-    for (int h = kClusterThreads / 64; h >= 1; h >>= 1)
-#pragma unroll
-      for (int w = 0; w < h; ++w) q[w] += q[w + h];
-    mine[threadIdx.x] = q[0];
-  }
-  cl.sync();
-  if (threadIdx.x < NV) {
-    // the 16 partials loaded at once, then added in a fixed pairwise tree
-    double q[kClusterCtas];
-#pragma unroll
-    for (int c = 0; c < kClusterCtas; ++c) q[c] = cl.map_shared_rank(mine, c)[threadIdx.x];
-#pragma unroll
-    for (int h = kClusterCtas / 2; h >= 1; h >>= 1)
-#pragma unroll
-      for (int c = 0; c < h; ++c) q[c] += q[c + h];
-    tot[threadIdx.x] = q[0];
-  }
-  __syncthreads();
-  round += 1;
-}
-
 
 // The solve.  One cluster; every CTA runs the same control flow on the same
 // scalars.  Outcome and counts are written to a.out by rank 0.
@@ -478,41 +422,10 @@ static int bcg_cluster_cap(int rpc, size_t bytes) {
 static bool bcg_cluster_fits(gsk_ctx* ctx, int n) {
   if (ctx->cluster_max_n < 0) {
     ctx->cluster_max_n = 0;
-    int optin = 0;
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    // dynamic shared memory: what the device allows a block, less the
-    // kernel's static shared memory
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, (const void*)bcg_cluster) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    optin -= (int)fa.sharedSizeBytes;
-    ctx->cluster_smem = optin;
-    const int rpc_max = (int)((optin / sizeof(double) - (16 + 64 + 8)) / (kClusterVecs + 1));
-    const void* k = (const void*)bcg_cluster;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = kClusterCtas;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(kClusterCtas);
-    cfg.blockDim = dim3(kClusterThreads);
-    cfg.dynamicSmemBytes = (size_t)optin;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.dynamicSmemBytes) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveClusters(&nclusters, (void*)bcg_cluster, &cfg) != cudaSuccess || nclusters < 1) {
-      cudaGetLastError();
-      return false;
-    }
+    const int smem = cluster_smem_limit(bcg_cluster, ctx->device);
+    if (smem <= 0) return false;
+    ctx->cluster_smem = smem;
+    const int rpc_max = (int)((smem / sizeof(double) - (16 + 64 + 8)) / (kClusterVecs + 1));
     ctx->cluster_max_n = rpc_max * kClusterCtas;
   }
   return n <= ctx->cluster_max_n && n <= ctx->small_n;
@@ -566,21 +479,9 @@ gsk_status bcg_cluster_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void
   a.cap = bcg_cluster_cap(a.rpc, (size_t)ctx->cluster_smem);
   a.out = dout;
   a.err = err;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = kClusterCtas;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(kClusterCtas);
-  cfg.blockDim = dim3(kClusterThreads);
-  cfg.dynamicSmemBytes = (size_t)ctx->cluster_smem;
-  cfg.stream = st;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
   GSK_CK(cudaEventRecord(ctx->ev0, st));
   GSK_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
-  GSK_CK(cudaLaunchKernelEx(&cfg, bcg_cluster, a));
+  GSK_CK(cluster_launch(bcg_cluster, a, (size_t)ctx->cluster_smem, st));
   GSK_CK(cudaEventRecord(ctx->ev1, st));
   if (!info) return GSK_OK;
   char* hp = (char*)ctx->host_pinned;

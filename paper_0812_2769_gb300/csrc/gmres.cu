@@ -363,6 +363,12 @@ extern "C" gsk_status gmres_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b,
   if (m < 1 || m > kMaxM) return ctx->fail(GSK_ERR_ARG, "m must be in 1..64");
   if (opts.precision == GSK_PREC_MIXED) return gmres_solve_mixed(ctx, A, b, x, m, tol, &opts, info, stream);
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    // small systems: the whole solve on one thread-block cluster
+    bool used = false;
+    s = gm_cluster_solve(ctx, A, b, x, m, tol, opts, info, st, &used);
+    if (used) return s;
+  }
   GmPlan P;
   if ((s = gm_prepare(ctx, A, b, x, m, tol, opts, P)) != GSK_OK) return s;
   if (A->n == 0) {

@@ -207,6 +207,12 @@ struct LaunchTimer {
 
 gsk_status bcg_cluster_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, double tol,
                              const gsk_opts& opts, gsk_info* info, cudaStream_t st, bool* used);
+// GMRES(m) on one thread-block cluster for small systems (cluster_gmres.cu);
+// *used = false when the system is not taken.  gm_cluster_rows: the most
+// rows it takes for restart length m.
+gsk_status gm_cluster_solve(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, int m, double tol,
+                            const gsk_opts& opts, gsk_info* info, cudaStream_t st, bool* used);
+int gm_cluster_rows(gsk_ctx* ctx, int m);
 gsk_status bcg_profile(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, double tol, const gsk_opts& opts,
                        int max_iters, LaunchTimer& T, gsk_info* info);
 gsk_status gm_profile(gsk_ctx* ctx, const gsk_csr* A, const void* b, void* x, int m, double tol,
