@@ -59,15 +59,17 @@ __device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, const double 
   __syncthreads();
   double* mine = red + (round & 1) * 8;
   if (threadIdx.x < NV) {
-    // the warps' sums in a fixed pairwise tree (a serial chain of FP64
-    // additions costs a full pipe pass per addition on this part)
+    // the warps' sums in a fixed pairwise tree over the nw warps that hold
+    // rows (the additions of the empty slots' zeros are skipped: the same
+    // sums, and on this part every FP64 instruction costs its pipe time)
     double q[kClusterThreads / 32];
 #pragma unroll
     for (int w = 0; w < kClusterThreads / 32; ++w) q[w] = w < nw ? wsum[w * NV + threadIdx.x] : 0.0;
 #pragma unroll
     for (int h = kClusterThreads / 64; h >= 1; h >>= 1)
 #pragma unroll
-      for (int w = 0; w < h; ++w) q[w] += q[w + h];
+      for (int w = 0; w < h; ++w)
+        if (w + h < nw) q[w] += q[w + h];
     mine[threadIdx.x] = q[0];
   }
   cl.sync();

@@ -20,9 +20,12 @@
 // or at maxit; then the back substitution, x += V (sig .* y) and the true
 // metric, which decides convergence, with tau tightened by tol / metric
 // when the estimate met tau but the metric did not.  Only the order of the
-// additions inside the sums differs.  The Hessenberg columns are kept
-// rotated (the triangle R of the least-squares problem), one copy per CTA:
-// the scalar work is done by thread 0 of every CTA on identical totals.
+// additions inside the sums differs, and the scalar recurrences multiply by
+// reciprocals and compare squares where the grid-wide solver divides and
+// takes roots (a lone thread's FP64 operation waits its whole latency on this
+// part).  The Hessenberg columns are kept rotated (the triangle R of the
+// least-squares problem), one copy per CTA: every CTA does the scalar work
+// itself on identical totals.
 #include <algorithm>
 #include <cfloat>
 
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) gm_cluster(ClusterGmArgs a
   const bool wid = a.wmode == 1 || (a.wmode == 0 && tot[1] == 0.0);
 
   __shared__ struct {
-    double mu0, rho0, tau, est, mu_true;
+    double mu0, rho0, inv_rho0, tau, est, mu_true;
     int iters, restarts, conv, kcols, est_hit, j, cont, stop;
   } sc;
   bool first = true;
@@ -215,6 +218,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) gm_cluster(ClusterGmArgs a
       if (first) {
         sc.mu0 = sqrt(tot[0]);
         sc.rho0 = rn;
+        sc.inv_rho0 = 1.0 / rn;
         sc.iters = 0;
         sc.restarts = 0;
         sc.tau = a.tol;
@@ -304,55 +308,74 @@ __global__ void __launch_bounds__(kClusterThreads, 1) gm_cluster(ClusterGmArgs a
         const double v1[1] = {an};
         cluster_sum<1>(cl, v1, red, wsum, tot, round, nw);  // also publishes V[:, j+1]
       }
-      // the Hessenberg column, the rotations and the cycle's tests
-      if (threadIdx.x == 0) {
-        for (int c = 0; c <= j; ++c) hs[c] = h1[c] + h2[c];
-        const double hnext = sqrt(tot[0]);
-        // ||A v_j||^2 = ||h1 + h2||^2 + hnext^2
-        double aw2 = hnext * hnext;
-        for (int c = 0; c <= j; ++c) aw2 = fma(hs[c], hs[c], aw2);
-        const double aw_norm = sqrt(aw2);
-        sc.iters += 1;
-        for (int q = 0; q < j; ++q) {
-          const double t0 = csn[q] * hs[q] + snn[q] * hs[q + 1];
-          const double t1 = -snn[q] * hs[q] + csn[q] * hs[q + 1];
-          hs[q] = t0;
-          hs[q + 1] = t1;
+      // the Hessenberg column, the rotations and the cycle's tests: warp 0
+      // forms h = h1 + h2 and ||h||^2 across its lanes; lane 0 applies the
+      // earlier rotations (a chain through the one carried entry, each
+      // rotated entry stored straight into R), forms the new rotation and
+      // takes the decisions.  A lone thread's FP64 operation waits its full
+      // latency on this part, so the chain keeps few of them: squared
+      // comparisons instead of roots, one reciprocal for c and s, and
+      // sqrt(a^2 + b^2) for hypot(a, b) where the squares are safe
+      if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double part = 0.0;
+        for (int c = lane; c <= j; c += 32) {
+          const double h = h1[c] + h2[c];
+          hs[c] = h;
+          part = fma(h, h, part);
         }
-        const double rho = hypot(hs[j], hnext);
-        double c_, s_;
-        if (rho == 0.0) {
-          c_ = 1.0;
-          s_ = 0.0;
-        } else {
-          c_ = hs[j] / rho;
-          s_ = hnext / rho;
+        const double hh = warp_allsum(part);  // ||h1 + h2||^2
+        __syncwarp();
+        if (lane == 0) {
+          const double hn2 = tot[0];
+          const double hnext = sqrt(hn2);
+          const double inv_hnext = 1.0 / hnext;
+          // ||A v_j||^2 = ||h1 + h2||^2 + hnext^2 (w's parts along the
+          // orthonormal basis and orthogonal to it)
+          const double aw2 = hh + hn2;
+          sc.iters += 1;
+          double* rc = R + (long long)j * (j + 1) / 2;
+          double hq = hs[0];
+          for (int q = 0; q < j; ++q) {
+            const double c = csn[q], s = snn[q], hn = hs[q + 1];
+            rc[q] = c * hq + s * hn;
+            hq = -s * hq + c * hn;
+          }
+          const double r2 = fma(hq, hq, hn2);
+          const double rho = (r2 > 1e-290 && r2 < 1e290) ? sqrt(r2) : hypot(hq, hnext);
+          double c_, s_;
+          if (rho == 0.0) {
+            c_ = 1.0;
+            s_ = 0.0;
+          } else {
+            const double inv = 1.0 / rho;
+            c_ = hq * inv;
+            s_ = hnext * inv;
+          }
+          csn[j] = c_;
+          snn[j] = s_;
+          rc[j] = rho;
+          const double gj = g[j];
+          g[j + 1] = -s_ * gj;
+          g[j] = c_ * gj;
+          const double est = fabs(g[j + 1]) * sc.inv_rho0;
+          sc.est = est;
+          sc.kcols = k;
+          int cont = 1;
+          if (est < sc.tau) {
+            sc.est_hit = 1;
+            cont = 0;
+          } else if (hn2 <= a.hbrk * a.hbrk * aw2) {  // hnext <= hbrk ||A v_j||
+            cont = 0;
+          } else if (k >= m || sc.iters >= a.maxit) {
+            cont = 0;
+          }
+          if (cont) {
+            sig[j + 1] = inv_hnext;
+            sc.j = j + 1;
+          }
+          sc.cont = cont;
         }
-        csn[j] = c_;
-        snn[j] = s_;
-        double* rc = R + (long long)j * (j + 1) / 2;
-        for (int q = 0; q < j; ++q) rc[q] = hs[q];
-        rc[j] = rho;
-        const double gj = g[j];
-        g[j + 1] = -s_ * gj;
-        g[j] = c_ * gj;
-        const double est = fabs(g[j + 1]) / sc.rho0;
-        sc.est = est;
-        sc.kcols = k;
-        int cont = 1;
-        if (est < sc.tau) {
-          sc.est_hit = 1;
-          cont = 0;
-        } else if (hnext <= a.hbrk * aw_norm) {
-          cont = 0;
-        } else if (k >= m || sc.iters >= a.maxit) {
-          cont = 0;
-        }
-        if (cont) {
-          sig[j + 1] = 1.0 / hnext;
-          sc.j = j + 1;
-        }
-        sc.cont = cont;
       }
       __syncthreads();
       if (!sc.cont) break;
