@@ -196,15 +196,33 @@ def test_full_c2_bicgstab_gs2_properties():
     assert np.linalg.norm(xg - s.x_true) / np.linalg.norm(s.x_true) < 1e-3
 
 
+def _path_ctx(path):
+    import os
+
+    g = gsk()
+    old = os.environ.get("GSK_SMALL_N")
+    os.environ["GSK_SMALL_N"] = "32768" if path == "cluster" else "0"
+    try:
+        return g.Context(0)
+    finally:
+        if old is None:
+            del os.environ["GSK_SMALL_N"]
+        else:
+            os.environ["GSK_SMALL_N"] = old
+
+
+@pytest.mark.parametrize("path", ["cluster", "grid"])
 @pytest.mark.parametrize("seed", [3, 11])
-def test_counts_match_the_oracle_exactly_where_rounding_does_not_matter(seed):
+def test_counts_match_the_oracle_exactly_where_rounding_does_not_matter(seed, path):
     """On well-conditioned nonsymmetric systems (the ones on which the oracle
     matches SciPy step for step) the GPU takes exactly the oracle's number of
     GMRES(m) steps and Bi-CGSTAB iterations, and reaches the same solution
-    to about the rounding of the summation order."""
+    to about the rounding of the summation order -- on the thread-block
+    cluster that takes systems this small, and on the grid-wide kernels."""
     import torch
 
     g = gsk()
+    ctx = _path_ctx(path)
     rs = np.random.default_rng(seed)
     n = 5000
     rows, cols, vals = [], [], []
@@ -225,12 +243,13 @@ def test_counts_match_the_oracle_exactly_where_rounding_does_not_matter(seed):
     for tol in (1e-6, 1e-12):
         for m in (5, 20):
             x = torch.zeros(n, dtype=torch.float64, device="cuda")
-            info = g.gmres_solve(A, bd, x, m=m, tol=tol, options=o)
+            info = g.gmres_solve(A, bd, x, m=m, tol=tol, options=o, ctx=ctx)
             xo, io = oracle.gmres(rp, ci, va, b, m=m, tol=tol, w=np.ones(n))
             assert info["conv"] == io["conv"] == 0 and info["iters"] == io["iters"], (m, tol, info, io)
             assert np.abs(x.cpu().numpy() - xo).max() <= 1e-11 * np.abs(xo).max()
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
-        info = g.bicgstab_solve(A, bd, x, tol=tol, options=o)
+        info = g.bicgstab_solve(A, bd, x, tol=tol, options=o, ctx=ctx)
         xo, io = oracle.bicgstab(rp, ci, va, b, tol=tol, refresh=0, w=np.ones(n))
         assert info["conv"] == io["conv"] == 0 and info["iters"] == io["iters"], (tol, info, io)
         assert np.abs(x.cpu().numpy() - xo).max() <= 1e-11 * np.abs(xo).max()
+    ctx.close()
