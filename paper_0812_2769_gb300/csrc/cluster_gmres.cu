@@ -268,13 +268,18 @@ __global__ void __launch_bounds__(kClusterThreads, 1) gm_cluster(ClusterGmArgs a
     if (sc.stop) break;
 
     // ---- the cycle's Arnoldi steps
+    bool ahead = false;  // this step's product was formed during the last step
     for (;;) {
       const int j = sc.j, k = j + 1;
       const double* vj = V + (long long)j * rpc;
       double* w = V + (long long)(j + 1) * rpc;
       const double sj = sig[j];
-      // w = A v_j
-      GC_ROWS(li) w[li] = sj * rowprod(li, vj);
+      // w = A v_j = sig[j] (A V[:, j]); A V[:, j] may already be in w
+      if (ahead) {
+        GC_ROWS(li) w[li] = sj * w[li];
+      } else {
+        GC_ROWS(li) w[li] = sj * rowprod(li, vj);
+      }
       __syncthreads();
       // pass 1: h1 = sig .* (V_k^T w)
       cluster_multidot(cl, V, w, rpc, nloc, k, redk, M1, tot, kround);
@@ -307,6 +312,14 @@ __global__ void __launch_bounds__(kClusterThreads, 1) gm_cluster(ClusterGmArgs a
         }
         const double v1[1] = {an};
         cluster_sum<1>(cl, v1, red, wsum, tot, round, nw);  // also publishes V[:, j+1]
+      }
+      // Meanwhile warps 1.. form the next step's product A V[:, j+1] (the
+      // column is final and visible, and its scale sig[j+1] only multiplies
+      // the sums) in V[:, j+2]; if the cycle ends here it is not used
+      ahead = j + 2 <= m;
+      if (ahead && threadIdx.x >= 32) {
+        double* wn = V + (long long)(j + 2) * rpc;
+        for (int li = threadIdx.x - 32; li < nloc; li += kClusterThreads - 32) wn[li] = rowprod(li, w);
       }
       // the Hessenberg column, the rotations and the cycle's tests: warp 0
       // forms h = h1 + h2 and ||h||^2 across its lanes; lane 0 applies the
