@@ -52,8 +52,9 @@ struct gsk_ctx {
   // more resident blocks hide less latency than they cost, as the second CGS
   // pass re-reads the basis rows of the first from L1 (measured best: 3)
   int basis_per_sm = 3;
-  // Bi-CGSTAB on one thread-block cluster for systems of at most small_n rows
-  // (GSK_SMALL_N overrides; 0 disables); cluster_max_n: the most rows the
+  // Bi-CGSTAB and GMRES on one thread-block cluster for systems of at most
+  // small_n rows that fit the cluster's shared memory (GSK_SMALL_N
+  // overrides; 0 disables); cluster_max_n: the most rows the Bi-CGSTAB
   // cluster kernel holds on this device (-1: not yet queried)
   int small_n = 32768;
   int cluster_max_n = -1;
