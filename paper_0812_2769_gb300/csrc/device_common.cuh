@@ -69,57 +69,53 @@ __device__ __forceinline__ T warp_allsum(T v) {
   return v;
 }
 
-// Block-wide sum of nv per-thread values held in shared memory as
+// Block-wide sum of nv <= 16 per-thread values held in shared memory as
 // tab[k * BLOCK + t] (the table is consumed), added in the table's type.
-// Result in res[k] (shared), valid after the call.  Tree as in block_sum.
+// Result in res[k] (shared), valid after the call.
+// On this part each SM sub-partition has a narrow FP64 unit and a warp's FP64
+// instruction costs its pipe time whatever its active lanes, so the work is
+// dealt over every warp instead of narrowing to one: each value's BLOCK
+// entries first fold to 32 (fold q adds entries q, q + 32, q + 64, ... in
+// that order; the nv * 32 folds are spread over all threads), then each warp
+// finishes two values, its half-warps adding folds l and l + 16 and meeting
+// in a fixed four-level shuffle tree.
 template <int BLOCK, typename TT>
 __device__ __forceinline__ void block_sum_table(TT* tab, int nv, double* res) {
+  static_assert(BLOCK % 32 == 0 && BLOCK >= 64, "block of whole warps, at least two");
   __syncthreads();
+  for (int o = threadIdx.x; o < nv * 32; o += BLOCK) {
+    TT* p = tab + (o >> 5) * BLOCK + (o & 31);
+    TT t = p[0];
 #pragma unroll
-  for (int s = BLOCK / 2; s >= 32; s >>= 1) {
-    if (threadIdx.x < s)
-      for (int k = 0; k < nv; ++k) tab[k * BLOCK + threadIdx.x] += tab[k * BLOCK + threadIdx.x + s];
-    __syncthreads();
+    for (int r = 1; r < BLOCK / 32; ++r) t += p[32 * r];
+    p[0] = t;  // each fold reads and writes only its own entries
   }
-  // the remaining 32 partial sums of each value: one warp per value
-  for (int k = warp_id(); k < nv; k += BLOCK / 32) {
-    const TT t = warp_allsum(tab[k * BLOCK + lane_id()]);
-    if (lane_id() == 0) res[k] = (double)t;
+  __syncthreads();
+  const int half = lane_id() >> 4, l = lane_id() & 15;
+  for (int v0 = 2 * warp_id(); v0 < nv; v0 += 2 * (BLOCK / 32)) {  // warp-uniform
+    const int v = v0 + half;
+    TT t = TT(0);
+    if (v < nv) t = tab[v * BLOCK + l] + tab[v * BLOCK + l + 16];
+#pragma unroll
+    for (int off = 8; off; off >>= 1) t += __shfl_xor_sync(kFull, t, off);
+    if (l == 0 && v < nv) res[v] = (double)t;
   }
   __syncthreads();
 }
 
 // Block-wide sum of NV register values (all threads contribute).  Uses the
-// caller's shared scratch sm[NV * BLOCK]; totals in res[NV] (shared).
-// The values go through a shared-memory tree (BLOCK/2, BLOCK/4, ... 32
-// active threads) and one warp finishes with shuffles: about 12 warp-wide
-// FP64 additions per value instead of 45 for a shuffle tree in every warp,
-// which matters on a part with little FP64 throughput.
-// The tree runs in the values' type A: FP64 for FP64 data, FP32 for the
-// FP32 inner solves (whose per-thread sums are FP32 already); the totals are
-// returned in FP64 for the grid-wide sum.
+// caller's shared scratch sm[NV * BLOCK]; totals in res[NV] (shared).  The
+// sum runs in the values' type A (FP64 for FP64 data, FP32 for the FP32
+// inner solves, whose per-thread sums are FP32 already), the same fixed
+// order as block_sum_table; the totals are returned in FP64 for the
+// grid-wide sum.
 template <int NV, int BLOCK, typename A>
 __device__ __forceinline__ void block_sum(const A (&v)[NV], A* sm, double* res) {
-  __syncthreads();
+  static_assert(NV <= 16, "at most 16 values per call");
+  __syncthreads();  // the scratch may still be read by an earlier sum
 #pragma unroll
   for (int k = 0; k < NV; ++k) sm[k * BLOCK + threadIdx.x] = v[k];
-  __syncthreads();
-#pragma unroll
-  for (int s = BLOCK / 2; s >= 32; s >>= 1) {
-    if (threadIdx.x < s) {
-#pragma unroll
-      for (int k = 0; k < NV; ++k) sm[k * BLOCK + threadIdx.x] += sm[k * BLOCK + threadIdx.x + s];
-    }
-    __syncthreads();
-  }
-  if (warp_id() == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      const A t = warp_allsum(sm[k * BLOCK + lane_id()]);
-      if (lane_id() == 0) res[k] = (double)t;
-    }
-  }
-  __syncthreads();
+  block_sum_table<BLOCK>(sm, NV, res);
 }
 
 // Grid-wide deterministic sum of nv block totals blk[k] (shared memory, valid
@@ -127,15 +123,20 @@ __device__ __forceinline__ void block_sum(const A (&v)[NV], A* sm, double* res) 
 // finishes last; that block then finds the totals in tot[k] (shared).  The
 // counter is reset so the site can be reused by the next launch.
 // One level: each block publishes its totals and counts itself in; the last
-// one sums all G partials of each value (one warp per value, lanes over the
-// partials in a fixed order, a fixed shuffle tree).  The serial tail of a
-// launch is then one fence, one atomic and one round of loads: a two-level
-// scheme (groups of blocks, then the group totals) measured longer, its
-// second atomic and fence sitting on the path that every other SM idles on.
+// one sums all G partials of each value with all its threads.  Value v's
+// partials go to tpv threads (the largest power of two up to 32 with
+// nv * tpv <= blockDim.x, so that a value's threads are neighbouring lanes of
+// one warp); thread q adds partials q, q + tpv, q + 2 tpv, ... in that order,
+// issuing their loads B at a time ahead of the additions (B = 16 in kernels
+// with many values, whose registers are free by then), and the tpv
+// sums meet in a fixed shuffle tree.  The serial tail of a launch is then one
+// fence, one atomic and a round or two of loads: a two-level scheme (groups
+// of blocks, then the group totals) measured longer, its second atomic and
+// fence sitting on the path that every other SM idles on.
+template <int B = 8>
 __device__ __forceinline__ bool grid_sum(const double* blk, int nv, const GridRed& R, double* tot) {
   __shared__ int s_last;
   const int G = gridDim.x, b = blockIdx.x;
-  const int nwarps = blockDim.x >> 5;
   if (threadIdx.x == 0) {
     for (int k = 0; k < nv; ++k) R.partials[k * G + b] = blk[k];
     __threadfence();
@@ -145,17 +146,24 @@ __device__ __forceinline__ bool grid_sum(const double* blk, int nv, const GridRe
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-  for (int k = warp_id(); k < nv; k += nwarps) {
-    const double* p = R.partials + (long long)k * G;
-    double v0 = 0.0, v1 = 0.0;
-    int q = lane_id();
-    for (; q + 32 < G; q += 64) {  // two independent chains, loads in flight together
-      v0 += __ldcg(p + q);
-      v1 += __ldcg(p + q + 32);
+  int tpv = 32;
+  while (tpv > 1 && tpv * nv > (int)blockDim.x) tpv >>= 1;
+  const int per_round = (int)blockDim.x / tpv;
+  for (int v0 = 0; v0 < nv; v0 += per_round) {  // one round unless nv > blockDim.x
+    const int v = v0 + (int)threadIdx.x / tpv, q = (int)threadIdx.x % tpv;
+    double s = 0.0;
+    if (v < nv) {
+      const double* p = R.partials + (long long)v * G;
+      for (int i = q; i < G; i += B * tpv) {
+        double t[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) t[u] = i + u * tpv < G ? __ldcg(p + i + u * tpv) : 0.0;
+#pragma unroll
+        for (int u = 0; u < B; ++u) s += t[u];
+      }
     }
-    if (q < G) v0 += __ldcg(p + q);
-    const double v = warp_allsum(v0 + v1);
-    if (lane_id() == 0) tot[k] = v;
+    for (int off = tpv >> 1; off; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+    if (v < nv && q == 0) tot[v] = s;
   }
   __syncthreads();
   if (threadIdx.x == 0) R.counters[0] = 0u;

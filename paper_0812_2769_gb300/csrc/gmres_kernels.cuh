@@ -39,7 +39,7 @@
 namespace gsk {
 
 struct GmState {
-  double rho0, mu0, tau, tol, est, mu_true, aw_norm, hbrk;
+  double rho0, mu0, tau, tol, est, mu_true, inv_rho0, hbrk;
   int m, maxit, iters, restarts, conv, j, kcols, stop, est_hit, w_identity, cont;
 };
 
@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(kBlock) gm_residual(GmArgs<T> a) {
       const double mu0 = sqrt(tot[0]);
       S->mu0 = mu0;
       S->rho0 = rn;
+      S->inv_rho0 = 1.0 / rn;
       S->iters = 0;
       S->restarts = 0;
       S->tau = S->tol;
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(kBlock) gm_gd(GmArgs<T> a) {
     }
   }
   block_sum_chunked<KP>(acc, k, table, res);
-  if (grid_sum(res, k, a.red, tot)) {
+  if (grid_sum<(KP >= 16 ? 16 : 8)>(res, k, a.red, tot)) {
     for (int c = threadIdx.x; c < k; c += kBlock) a.h1[c] = a.sig[c] * tot[c];
   }
 }
@@ -344,23 +345,61 @@ __global__ void __launch_bounds__(kBlock) gm_gb(GmArgs<T> a) {
     }
   }
   block_sum_chunked<KP>(acc, k, table, res);
-  if (grid_sum(res, k, a.red, tot)) {
+  if (grid_sum<(KP >= 16 ? 16 : 8)>(res, k, a.red, tot)) {
     for (int c = threadIdx.x; c < k; c += kBlock) a.h2[c] = a.sig[c] * tot[c];
   }
 }
 
 // CGS pass 3: w -= V_k (sig .* h2); ||w||; then the Hessenberg column, the
-// Givens rotations and the cycle's stopping tests (one thread).
+// Givens rotations and the cycle's stopping tests.
+//
+// Every block stages, at entry, what the closing block will need (the
+// column h = h1 + h2, the earlier rotations, g_j and the state's scalars):
+// the loads are a few hundred bytes per block from L2 and complete during
+// the pass, so the closing block starts its scalar work with no memory
+// round trip.  There warp 0 forms ||h||^2 and the products c_q h_{q+1}
+// across its lanes while warp 1 forms hnext = ||w|| and 1/hnext; lane 0 of
+// warp 0 then applies the earlier rotations as a chain of one FMA per
+// rotation through the one carried entry (the rotated entries themselves are
+// formed afterwards by all threads at once), forms the new rotation and
+// takes the decisions.  A lone thread's FP64 instruction waits its full
+// latency on this part, so the chain keeps few of them: squared comparisons
+// instead of roots, one reciprocal for c and s, 1/rho0 kept in the state,
+// and sqrt(a^2 + b^2) for hypot(a, b) where the squares are safe.
+struct GcStage {
+  double gj, inv_rho0, tau, hbrk, hh, hnext, inv_hnext;
+  int iters, maxit, err;
+};
+
 template <typename T, int KP>
 __global__ void __launch_bounds__(kBlock) gm_gc(GmArgs<T> a) {
   using Acc = typename AccOf<T>::type;
   __shared__ Acc coef[KP];
   __shared__ double table[kBlock], res[1], tot[1];
+  __shared__ double hs[kMaxM + 1], css[kMaxM], sns[kMaxM], chq[kMaxM], hcar[kMaxM];
+  __shared__ GcStage st;
   GmState* S = a.S;
   if (a.unrolled && !S->cont) return;  // the cycle ended at an earlier step
   const int j = S->j, k = j + 1;
   T* wv = a.V + (long long)(j + 1) * a.ldv;
-  for (int c = threadIdx.x; c < k; c += kBlock) coef[c] = (Acc)(a.sig[c] * a.h2[c]);
+  for (int c = threadIdx.x; c < k; c += kBlock) {
+    const double h2 = a.h2[c];
+    coef[c] = (Acc)(a.sig[c] * h2);
+    hs[c] = a.h1[c] + h2;
+    if (c < j) {
+      css[c] = a.cs[c];
+      sns[c] = a.sn[c];
+    }
+  }
+  if (threadIdx.x == 0) {
+    st.gj = a.g[j];
+    st.inv_rho0 = S->inv_rho0;
+    st.tau = S->tau;
+    st.hbrk = S->hbrk;
+    st.iters = S->iters;
+    st.maxit = S->maxit;
+    st.err = *(volatile int*)a.err;  // set by earlier kernels only: this one flags nothing
+  }
   __syncthreads();
   constexpr int R = Vec16<T>::R;
   Acc acc[1] = {Acc(0)};
@@ -395,74 +434,79 @@ __global__ void __launch_bounds__(kBlock) gm_gc(GmArgs<T> a) {
   const double accd[1] = {(double)acc[0]};
   block_sum<1, kBlock>(accd, table, res);
   if (!grid_sum(res, 1, a.red, tot)) return;
-  // The closing block: the Hessenberg column h1 + h2 and the earlier
-  // rotations are gathered into shared memory by all its threads at once;
-  // one thread then rotates there (a serial walk over global memory would
-  // pay a memory round trip per column).
-  __shared__ double hs[kMaxM + 2], css[kMaxM], sns[kMaxM];
+  // the closing block
   const int ld = a.m + 1;
-  for (int c = threadIdx.x; c <= j; c += kBlock) {
-    const double h = a.h1[c] + a.h2[c];
-    hs[c] = h;
-    if (a.Hraw) a.Hraw[(long long)j * ld + c] = h;
-    if (c < j) {
-      css[c] = a.cs[c];
-      sns[c] = a.sn[c];
+  const double hn2 = tot[0];
+  if (threadIdx.x < 32) {
+    double part = 0.0;
+    for (int c = threadIdx.x; c <= j; c += 32) {
+      part = fma(hs[c], hs[c], part);
+      if (c < j) chq[c] = css[c] * hs[c + 1];
+      if (a.Hraw) a.Hraw[(long long)j * ld + c] = hs[c];
     }
+    const double hh = warp_allsum(part);  // ||h1 + h2||^2
+    if (threadIdx.x == 0) st.hh = hh;
+  } else if (threadIdx.x == 32) {
+    const double hnext = sqrt(hn2);
+    st.hnext = hnext;
+    st.inv_hnext = 1.0 / hnext;
+    if (a.Hraw) a.Hraw[(long long)j * ld + j + 1] = hnext;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double* hcol = a.H + (long long)j * ld;
-    const double hnext = sqrt(tot[0]);
-    if (a.Hraw) a.Hraw[(long long)j * ld + j + 1] = hnext;
+    const double hnext = st.hnext;
     // ||A v_j||^2 = ||h1 + h2||^2 + hnext^2 (w's parts along the orthonormal
     // basis and orthogonal to it)
-    double aw2 = hnext * hnext;
-    for (int c = 0; c <= j; ++c) aw2 = fma(hs[c], hs[c], aw2);
-    S->aw_norm = sqrt(aw2);
-    S->iters += 1;
+    const double aw2 = st.hh + hn2;
+    const int iters = st.iters + 1;
+    S->iters = iters;
+    double hq = hs[0];
     for (int q = 0; q < j; ++q) {
-      const double t0 = css[q] * hs[q] + sns[q] * hs[q + 1];
-      const double t1 = -sns[q] * hs[q] + css[q] * hs[q + 1];
-      hs[q] = t0;
-      hs[q + 1] = t1;
+      hcar[q] = hq;  // the entry carried into rotation q
+      hq = fma(-sns[q], hq, chq[q]);
     }
-    const double rho = hypot(hs[j], hnext);
+    const double r2 = fma(hq, hq, hn2);
+    const double rho = (r2 > 1e-290 && r2 < 1e290) ? sqrt(r2) : hypot(hq, hnext);
     double c_, s_;
     if (rho == 0.0) {
       c_ = 1.0;
       s_ = 0.0;
     } else {
-      c_ = hs[j] / rho;
-      s_ = hnext / rho;
+      const double inv = 1.0 / rho;
+      c_ = hq * inv;
+      s_ = hnext * inv;
     }
     a.cs[j] = c_;
     a.sn[j] = s_;
-    for (int q = 0; q < j; ++q) hcol[q] = hs[q];
     hcol[j] = rho;
     hcol[j + 1] = 0.0;
-    const double gj = a.g[j];
-    a.g[j + 1] = -s_ * gj;
+    const double gj = st.gj;
+    const double gn = -s_ * gj;
+    a.g[j + 1] = gn;
     a.g[j] = c_ * gj;
-    const double est = fabs(a.g[j + 1]) / S->rho0;
+    const double est = fabs(gn) * st.inv_rho0;
     S->est = est;
     S->kcols = k;
     int cont = 1;
-    if (est < S->tau) {
+    if (est < st.tau) {
       S->est_hit = 1;
       cont = 0;
-    } else if (hnext <= S->hbrk * S->aw_norm) {
+    } else if (hn2 <= st.hbrk * st.hbrk * aw2) {  // hnext <= hbrk ||A v_j||
       cont = 0;
-    } else if (k >= a.m || S->iters >= S->maxit || *(volatile int*)a.err) {
+    } else if (k >= a.m || iters >= st.maxit || st.err) {
       cont = 0;
     }
     if (cont) {
-      a.sig[j + 1] = 1.0 / hnext;
+      a.sig[j + 1] = st.inv_hnext;
       S->j = j + 1;
     }
     S->cont = cont;
     if (!a.unrolled) gm_set_cond(a, a.h_inner, (unsigned)cont);
   }
+  __syncthreads();
+  // the rotated entries of column j above the diagonal
+  for (int q = threadIdx.x; q < j; q += kBlock) a.H[(long long)j * ld + q] = css[q] * hcar[q] + sns[q] * hs[q + 1];
 }
 
 // Back substitution H(0:k, 0:k) y = g(0:k), bottom row first, by one warp:

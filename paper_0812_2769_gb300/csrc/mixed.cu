@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(kBlock) mx_prep_gm(MxArgs a) {
     a.g[0] = beta;
     for (int q = 1; q <= a.m; ++q) a.g[q] = 0.0;
     Sg->rho0 = beta;
+    Sg->inv_rho0 = 1.0 / beta;
     Sg->j = 0;
     Sg->iters = 0;
     Sg->kcols = 0;
