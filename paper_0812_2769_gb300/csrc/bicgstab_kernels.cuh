@@ -136,7 +136,14 @@ __global__ void __launch_bounds__(kBlock) bcg_k1(BcgArgs<T> a) {
   BcgState* S = a.S;
   if (S->stop || S->check) return;
   __shared__ PipeSmem<T> pipe;
-  __shared__ double blk[2], tot[2];
+  __shared__ double blk[2], tot[2], sc[3];
+  // the scalars of the closing decision, loaded at entry (their round trip
+  // overlaps the product) into shared memory (no registers held meanwhile)
+  if (threadIdx.x == 0) {
+    sc[0] = S->brk;
+    sc[1] = S->rhn;
+    sc[2] = S->rho;
+  }
   double* sm = reinterpret_cast<double*>(&pipe);  // reduction scratch after the product
   using Acc = typename AccOf<T>::type;
   const T* __restrict__ rh = a.rh;
@@ -152,11 +159,11 @@ __global__ void __launch_bounds__(kBlock) bcg_k1(BcgArgs<T> a) {
     const double sigma = tot[0], vn = sqrt(tot[1]);
     if (*(volatile int*)a.err) {
       S->stop = 1;
-    } else if (!(fabs(sigma) > S->brk * S->rhn * vn)) {
+    } else if (!(fabs(sigma) > sc[0] * sc[1] * vn)) {
       S->conv = GSK_BREAKDOWN;
       S->stop = 1;
     } else {
-      S->alpha = S->rho / sigma;
+      S->alpha = sc[2] / sigma;
     }
   }
 }
@@ -207,7 +214,11 @@ __global__ void __launch_bounds__(kBlock) bcg_k2b(BcgArgs<T> a) {
   BcgState* S = a.S;
   if (S->stop || S->check) return;
   __shared__ PipeSmem<T> pipe;
-  __shared__ double blk[3], tot[3];
+  __shared__ double blk[3], tot[3], sc[2];
+  if (threadIdx.x == 0) {  // the closing decision's scalars, loaded at entry
+    sc[0] = S->mu0;
+    sc[1] = S->tol;
+  }
   double* sm = reinterpret_cast<double*>(&pipe);  // reduction scratch after the product
   using Acc = typename AccOf<T>::type;
   Acc acc[3] = {Acc(0), Acc(0), Acc(0)};
@@ -215,11 +226,11 @@ __global__ void __launch_bounds__(kBlock) bcg_k2b(BcgArgs<T> a) {
   else bcg_k2b_rows<false>(a, pipe, acc);
   block_sum<3, kBlock>(acc, reinterpret_cast<Acc*>(sm), blk);
   if (grid_sum(blk, 3, a.red, tot) && threadIdx.x == 0) {
-    const double mus = sqrt(tot[2]) / S->mu0;
+    const double mus = sqrt(tot[2]) / sc[0];
     S->mu_s = mus;
     if (*(volatile int*)a.err) {
       S->stop = 1;
-    } else if (mus < S->tol) {
+    } else if (mus < sc[1]) {
       S->halfexit = 1;  // x += alpha p in k3; this t is not used
     } else if (!(tot[1] > 0.0)) {
       S->conv = GSK_BREAKDOWN;
@@ -300,7 +311,19 @@ __global__ void __launch_bounds__(kBlock) bcg_k3(BcgArgs<T> a) {
     }
     return;
   }
-  __shared__ double sm[3 * kBlock], blk[3], tot[3];
+  __shared__ double sm[3 * kBlock], blk[3], tot[3], sc[8];
+  __shared__ int si[2];
+  if (threadIdx.x == 0) {  // the closing decision's scalars, loaded at entry
+    sc[0] = S->mu0;
+    sc[1] = S->tol;
+    sc[2] = S->omega;
+    sc[3] = S->brk;
+    sc[4] = S->rhn;
+    sc[5] = S->rho;
+    sc[6] = S->alpha;
+    si[0] = S->iters;
+    si[1] = S->maxit;
+  }
   const Acc omega = (Acc)S->omega;
   const bool wid = S->w_identity;
   Acc acc[3] = {Acc(0), Acc(0), Acc(0)};
@@ -308,26 +331,27 @@ __global__ void __launch_bounds__(kBlock) bcg_k3(BcgArgs<T> a) {
   else bcg_k3_rows<false, PRE>(a, alpha, omega, acc);
   block_sum<3, kBlock>(acc, reinterpret_cast<Acc*>(sm), blk);
   if (grid_sum(blk, 3, a.red, tot) && threadIdx.x == 0) {
-    S->iters += 1;
-    const double mur = sqrt(tot[1]) / S->mu0;
+    const int iters = si[0] + 1;
+    S->iters = iters;
+    const double mur = sqrt(tot[1]) / sc[0];
     S->mu_rec = mur;
     int check = 0, stop = 0;
-    if (mur < S->tol) {
+    if (mur < sc[1]) {
       check = 1;
-    } else if (S->omega == 0.0) {
+    } else if (sc[2] == 0.0) {
       S->conv = GSK_BREAKDOWN;
       stop = 1;
     } else {
       const double rho1 = tot[0], rn = sqrt(wid ? tot[1] : tot[2]);
-      if (!(fabs(rho1) > S->brk * S->rhn * rn)) {
+      if (!(fabs(rho1) > sc[3] * sc[4] * rn)) {
         S->conv = GSK_BREAKDOWN;
         stop = 1;
       } else {
-        S->beta = (rho1 / S->rho) * (S->alpha / S->omega);
+        S->beta = (rho1 / sc[5]) * (sc[6] / sc[2]);
         S->rho = rho1;
       }
     }
-    if (!check && !stop && S->iters >= S->maxit) {
+    if (!check && !stop && iters >= si[1]) {
       S->conv = GSK_MAXIT;
       stop = 1;
     }
