@@ -68,7 +68,7 @@ struct BatchParams {
 
 template <int NV, int BS>
 __device__ __forceinline__ void bsum(const double (&v)[NV], double* sm, double* res) {
-  block_sum<NV, BS>(v, sm, res);
+  block_sum_tree<NV, BS>(v, sm, res);
 }
 
 // y = A x for one system, thread per row; bad indices flag *err.

@@ -118,6 +118,35 @@ __device__ __forceinline__ void block_sum(const A (&v)[NV], A* sm, double* res) 
   block_sum_table<BLOCK>(sm, NV, res);
 }
 
+// Block-wide sum of NV register values with the shortest dependent chain
+// and few registers, for block sums on a latency-bound path (the batched
+// solvers, one block per system): a shared-memory tree (BLOCK/2, BLOCK/4,
+// ... 32 active threads) and one warp's shuffle tree.  Uses the caller's
+// shared scratch sm[NV * BLOCK]; totals in res[NV] (shared).
+template <int NV, int BLOCK, typename A>
+__device__ __forceinline__ void block_sum_tree(const A (&v)[NV], A* sm, double* res) {
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) sm[k * BLOCK + threadIdx.x] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int s = BLOCK / 2; s >= 32; s >>= 1) {
+    if (threadIdx.x < s) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sm[k * BLOCK + threadIdx.x] += sm[k * BLOCK + threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (warp_id() == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const A t = warp_allsum(sm[k * BLOCK + lane_id()]);
+      if (lane_id() == 0) res[k] = (double)t;
+    }
+  }
+  __syncthreads();
+}
+
 // Grid-wide deterministic sum of nv block totals blk[k] (shared memory, valid
 // in every thread).  Returns true in every thread of the one block that
 // finishes last; that block then finds the totals in tot[k] (shared).  The
