@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace gsk {
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -289,6 +291,70 @@ __device__ __forceinline__ double rsqrt_pos(double s) {
   return fma(y, e * fma(0.375, e, 0.5), y);
 }
 
+// Sums of |a| and of a^2 over a row of doubles in the integer pipes.  On
+// this part a row of GS(2) needs about 20 FP64 instructions (squares,
+// scaling products, the reciprocal square root) for 88 bytes of traffic, so
+// the FP64 pipe, not HBM, bounds the one-pass kernel; the sums move to the
+// integer units, which are many times wider.  Every entry a = m 2^(E-1075)
+// (m the 53-bit significand, E the biased exponent; subnormals have E = 0
+// and no implicit bit, and are taken as E = 1) is aligned to the row's
+// largest biased exponent emax and added as an integer: |a| as
+// (m 2^48) >> (emax - E) into a 128-bit accumulator with unit 2^(emax -
+// 1123), a^2 as the square of the 64-bit (m 2^5) >> (emax - E) (one wide
+// multiply, no 128-bit shift) with unit 2^(2 emax - 2160).  The only loss is
+// the bits shifted out below the unit (against a largest term of at least
+// 2^100 or 2^114 units), so the sum is the exact one to within a relative
+// len 2^-55 (a^2) or len 2^-100 (|a|) before its final rounding to double,
+// closer than an FP64 loop; the accumulators hold rows of up to 4,096 (a^2)
+// and 2^20 (|a|) entries, longer rows take the FP64 route.  `int_sum_to_double` rounds it to the nearest double; the callers
+// use these only where that double is normal (the row's largest exponent is
+// far from the ends of the range).
+__device__ __forceinline__ double int_sum_to_double(unsigned __int128 acc, int unit_exp) {
+  // acc > 0; value = acc 2^unit_exp
+  const unsigned long long hi = (unsigned long long)(acc >> 64), lo = (unsigned long long)acc;
+  const int lead = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  unsigned long long mant;
+  int shift = lead - 52;  // bits below the 53 kept
+  if (shift <= 0) {
+    mant = lo << (-shift);
+  } else {
+    mant = (unsigned long long)(acc >> shift);
+    const unsigned __int128 rem = acc & ((((unsigned __int128)1) << shift) - 1);
+    const unsigned __int128 half = ((unsigned __int128)1) << (shift - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      mant += 1ull;
+      if (mant >> 53) {
+        mant >>= 1;
+        shift += 1;
+      }
+    }
+  }
+  const long long ef = (long long)shift + unit_exp + 52 + 1023;  // biased exponent of mant 2^(shift + unit_exp)
+  return __longlong_as_double((ef << 52) | (long long)(mant & 0x000fffffffffffffull));
+}
+
+// sum |a_k| (P2 false) or sum a_k^2 (P2 true) over a row of doubles whose
+// largest magnitude has biased exponent emax (1 <= emax <= 2046).
+template <bool P2>
+__device__ __forceinline__ double row_int_sum(const double* v, int len, int emax) {
+  unsigned __int128 acc = 0;
+  for (int k = 0; k < len; ++k) {
+    const unsigned long long b = dbits(v[k]);
+    const int E = (int)((b >> 52) & 0x7ffull);
+    const unsigned long long m = (b & 0x000fffffffffffffull) | ((unsigned long long)(E != 0) << 52);
+    const int d = emax - (E == 0 ? 1 : E);  // >= 0
+    if (P2) {
+      if (d < 58) {
+        const unsigned long long q = (m << 5) >> d;
+        acc += (unsigned __int128)q * q;
+      }
+    } else {
+      if (d < 101) acc += ((unsigned __int128)m << 48) >> d;
+    }
+  }
+  return P2 ? int_sum_to_double(acc, 2 * emax - 2160) : int_sum_to_double(acc, emax - 1123);
+}
+
 // The rare cases of row_inv_norm, out of line so that the common path keeps
 // few registers: a row whose largest exponent e is far from 0 (its sum could
 // overflow or lose the small terms) and general p.  The row is summed again
@@ -328,6 +394,10 @@ __device__ __noinline__ double row_inv_norm_rescaled(const T* v, int len, int pm
 template <int PM, typename T>
 __device__ __forceinline__ double row_inv_norm_pm(const T* v, int len, double p, int* err) {
   constexpr int pmode = PM;
+  // FP64 rows take the sums of |a| and a^2 in the integer pipes (a second
+  // sweep over the row once its largest exponent is known); FP32 rows sum in
+  // FP64 as they go
+  constexpr bool kIntSum = std::is_same<T, double>::value && (PM == kP1 || PM == kP2);
   unsigned long long mb = 0ull;  // largest |a| (its bit pattern)
   unsigned long long nf = 0ull;  // nonzero when an entry is Inf or NaN
   double s = 0.0;
@@ -336,8 +406,10 @@ __device__ __forceinline__ double row_inv_norm_pm(const T* v, int len, double p,
     const unsigned long long bits = dbits(a) & 0x7fffffffffffffffull;
     nf |= (bits + 0x0010000000000000ull) & 0x8000000000000000ull;  // exponent field all ones
     mb = bits > mb ? bits : mb;
-    if (pmode == kP1) s += fabs(a);
-    else if (pmode == kP2) s = fma(a, a, s);
+    if (!kIntSum) {
+      if (pmode == kP1) s += fabs(a);
+      else if (pmode == kP2) s = fma(a, a, s);
+    }
   }
   if (nf) {
     atomicOr(err, kErrNonFinite);
@@ -349,9 +421,11 @@ __device__ __forceinline__ double row_inv_norm_pm(const T* v, int len, double p,
   }
   const int e = (int)(mb >> 52) - 1023;  // exponent of the largest magnitude
   double d;
-  if (pmode == kP2 && e > -480 && e < 480) {
+  if (pmode == kP2 && e > -480 && e < 480 && len < (1 << 12)) {
+    if constexpr (kIntSum) s = row_int_sum<true>(reinterpret_cast<const double*>(v), len, e + 1023);
     d = rsqrt_pos(s);
   } else if (pmode == kP1 && e > -1000 && e < 1000 && len < (1 << 20)) {
+    if constexpr (kIntSum) s = row_int_sum<false>(reinterpret_cast<const double*>(v), len, e + 1023);
     d = recip_pos(s);
   } else if (pmode == kPInf && e > -1000 && e < 1000) {
     d = recip_pos(__longlong_as_double((long long)mb));
