@@ -294,8 +294,11 @@ done:
 // GS(p) of one system in place (norms first, then the scaling only if no
 // row is zero or non-finite); then the metric weights W2 = 1/||a_i||_2 of the
 // scaled rows into w2 (left unused when p = 2: the rows then have unit norm).
-// Returns false (and the status) on an input error.
-template <int BS>
+// Returns false (and the status) on an input error.  INT_SUM: the row sums
+// in the integer pipes (row_inv_norm_pm); measured on the 4,096-system batch
+// it pays in the mixed-precision kernel (484 against 531 ms) and not in the
+// FP64 one (572 against 455 ms), so each kernel takes its faster form.
+template <int BS, bool INT_SUM>
 __device__ bool block_gs(const BatchSys& S, double* d, double* w2, bool need_w2, int* status) {
   __shared__ int s_err;
   if (threadIdx.x == 0) s_err = 0;
@@ -308,7 +311,7 @@ __device__ bool block_gs(const BatchSys& S, double* d, double* w2, bool need_w2,
       atomicOr(&s_err, kErrIndex);
       continue;
     }
-    if (scale) d[i] = row_inv_norm(S.val + rs, re - rs, pm, S.p, &s_err);
+    if (scale) d[i] = row_inv_norm<INT_SUM>(S.val + rs, re - rs, pm, S.p, &s_err);
     const unsigned long long bb = (unsigned long long)__double_as_longlong(S.b[i]);
     if ((bb & 0x7ff0000000000000ull) == 0x7ff0000000000000ull) atomicOr(&s_err, kErrNonFinite);
   }
@@ -324,7 +327,7 @@ __device__ bool block_gs(const BatchSys& S, double* d, double* w2, bool need_w2,
       for (int k = rs; k < re; ++k) S.val[k] *= di;
       S.b[i] *= di;
     }
-    if (need_w2) w2[i] = row_inv_norm(S.val + rs, re - rs, kP2, 2.0, &s_err);
+    if (need_w2) w2[i] = row_inv_norm<INT_SUM>(S.val + rs, re - rs, kP2, 2.0, &s_err);
   }
   __syncthreads();
   if (s_err) {
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(BS, (batch_min_blocks<BS, MIXED>())) batch_bic
     double* w2 = d + n;
     // after GS(2) the rows have unit norm: the metric weights are the identity
     const bool w_identity = P.metric_plain || S.p == 2.0;
-    const bool ok = block_gs<BS>(S, d, w2, !w_identity || MIXED, &o.status);
+    const bool ok = block_gs<BS, MIXED>(S, d, w2, !w_identity || MIXED, &o.status);
     if (ok) {
       if (!MIXED) {
         double* v = w2 + n;
@@ -675,7 +678,7 @@ __global__ void __launch_bounds__(BS) batch_gmres(BatchParams P) {
     double* d = reinterpret_cast<double*>(slot);
     double* w2 = d + n;
     const bool w_identity = P.metric_plain || S.p == 2.0;
-    const bool ok = block_gs<BS>(S, d, w2, !w_identity, &o.status);
+    const bool ok = block_gs<BS, false>(S, d, w2, !w_identity, &o.status);
     if (ok) {
       GmWork W;
       W.V = w2 + n;

@@ -391,13 +391,16 @@ __device__ __noinline__ double row_inv_norm_rescaled(const T* v, int len, int pm
 // definition up to rounding.  A non-finite entry, an all-zero row or a norm
 // whose reciprocal is not a finite double (every entry below 2^-1024) records
 // an error bit in *err and returns 0 (the row is then not scaled).
-template <int PM, typename T>
+template <int PM, typename T, bool INT_SUM = true>
 __device__ __forceinline__ double row_inv_norm_pm(const T* v, int len, double p, int* err) {
   constexpr int pmode = PM;
   // FP64 rows take the sums of |a| and a^2 in the integer pipes (a second
-  // sweep over the row once its largest exponent is known); FP32 rows sum in
-  // FP64 as they go
-  constexpr bool kIntSum = std::is_same<T, double>::value && (PM == kP1 || PM == kP2);
+  // sweep over the row once its largest exponent is known); FP32 rows, and
+  // callers that pass INT_SUM = false (the FP64 batched kernels, whose
+  // threads walk many rows from global memory one after another, where the
+  // second sweep's latency costs more than the FP64 it saves), sum in FP64
+  // as they go
+  constexpr bool kIntSum = INT_SUM && std::is_same<T, double>::value && (PM == kP1 || PM == kP2);
   unsigned long long mb = 0ull;  // largest |a| (its bit pattern)
   unsigned long long nf = 0ull;  // nonzero when an entry is Inf or NaN
   double s = 0.0;
@@ -440,13 +443,13 @@ __device__ __forceinline__ double row_inv_norm_pm(const T* v, int len, double p,
 }
 
 // The same with p chosen at run time (the one-block batched solvers).
-template <typename T>
+template <bool INT_SUM = true, typename T>
 __device__ __forceinline__ double row_inv_norm(const T* v, int len, int pmode, double p, int* err) {
   switch (pmode) {
-    case kP1: return row_inv_norm_pm<kP1>(v, len, p, err);
-    case kP2: return row_inv_norm_pm<kP2>(v, len, p, err);
-    case kPInf: return row_inv_norm_pm<kPInf>(v, len, p, err);
-    default: return row_inv_norm_pm<kPGen>(v, len, p, err);
+    case kP1: return row_inv_norm_pm<kP1, T, INT_SUM>(v, len, p, err);
+    case kP2: return row_inv_norm_pm<kP2, T, INT_SUM>(v, len, p, err);
+    case kPInf: return row_inv_norm_pm<kPInf, T, INT_SUM>(v, len, p, err);
+    default: return row_inv_norm_pm<kPGen, T, INT_SUM>(v, len, p, err);
   }
 }
 
