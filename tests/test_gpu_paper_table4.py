@@ -4,7 +4,14 @@ and the "limit" table (40^3, D = 1e4, convection 100 .. 1000), with the
 rows, bands and shortened "no convergence" runs of the oracle's test
 (test_paper_table4, which also lists the rows left out and why).  Restarted
 GMRES(10) is stable on these systems, so its GPU counts are also held to the
-oracle's within 1%."""
+oracle's within 1%.  Bi-CGSTAB's counts with GS at the tighter tolerances
+are decided by rounding (the oracle's own one-ulp ensembles, recorded in
+tests/golden/table4_bicgstab_ensembles.json, spread by up to half their
+size): a GPU count counts as matching when it lies in the band around the
+printed count or inside the recorded spread."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -18,6 +25,19 @@ pytestmark = pytest.mark.gpu
 NOCONV_MAXIT = 300
 EPS = np.finfo(np.float64).eps
 ROWS = [r for r in pt.load(pt.FIXTURE4) if not (r["scaling"] == "none" and r["precond"] == "ilut")]
+ENSEMBLES = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                        "table4_bicgstab_ensembles.json")))
+
+
+def _in_ensemble(row, tol, conv, iters):
+    """A converged Bi-CGSTAB count inside the oracle's recorded rounding
+    spread for this row (GS-scaled rows only), with the margin the other
+    ensemble tests use (5% or 2 iterations)."""
+    e = ENSEMBLES.get(f"{row['case']} {row['precond']} {tol:g}") if row["solver"] == "bicgstab" else None
+    if e is None or row["scaling"] != "gs" or not conv:
+        return False
+    lo, hi = e["min"], e["max"]
+    return min(0.95 * lo, lo - 2) <= iters <= max(1.05 * hi, hi + 2)
 _SYS = {}
 
 
@@ -59,7 +79,9 @@ def test_gpu_matches_table4(row, tol):
     printed = row["entries"][tol]
     maxit = NOCONV_MAXIT if printed == "noconv" else 10000
     conv, iters, relres = _gpu(s, row["solver"], row["scaling"], row["precond"], tol, maxit, row["m"] or 10)
-    assert pt.matches(row["solver"], printed, conv, iters, relres), (printed, conv, iters, relres)
+    ok = pt.matches(row["solver"], printed, conv, iters, relres)
+    ok = ok or (isinstance(printed, int) and _in_ensemble(row, tol, conv, iters))
+    assert ok, (printed, conv, iters, relres)
     if row["solver"] == "gmres" and isinstance(printed, int):
         if row["scaling"] == "gs":
             val, b, _ = oracle.gs_scale(s.rowptr, s.colidx, s.val, s.b, 2.0)

@@ -24,6 +24,9 @@ Rows left out, and why (the rest of this module holds them to the paper):
   1e-10 over a rounding ensemble, and the test checks that the paper's 1e-10
   is among them.
 * "limit" rows with ILU: not checked on the CPU (see test_gpu_ilu)."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -143,3 +146,25 @@ def test_limit_bicgstab_outcome_is_decided_by_rounding(conv):
         vv = val if k == 0 else val * (1.0 + rs.uniform(-2, 2, len(val)) * EPS)
         outcomes.append(_solve(s, vv, bb, "bicgstab", None, 1e-10, 10000)["conv"])
     assert oracle.CONVERGED in outcomes and oracle.BREAKDOWN in outcomes, outcomes
+
+
+# ------------------------------------------------- rounding ensembles
+def test_recorded_ensembles_contain_the_printed_counts():
+    """The oracle's one-ulp rounding ensembles of the GS-scaled Bi-CGSTAB rows
+    (tests/golden/table4_bicgstab_ensembles.json, written by the committed
+    script beside it from oracle/ alone): every member converges, and the
+    band around each printed count meets the recorded spread, so the paper's
+    run reads as one member of the same spread.  Where the spread is wider
+    than the band, a count outside the band is no evidence against a path
+    that takes this method's arithmetic (the GPU test accepts the spread)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table4_bicgstab_ensembles.json")
+    ens = json.load(open(path))
+    rows = [r for r in ROWS if r["solver"] == "bicgstab" and r["scaling"] == "gs"]
+    assert len(rows) == 4
+    for r in rows:
+        for tol in pt.TOLS:
+            e = ens[f"{r['case']} {r['precond']} {tol:g}"]
+            assert len(e["iters"]) == 16 and set(e["conv"]) == {oracle.CONVERGED}
+            assert e["min"] == min(e["iters"]) and e["max"] == max(e["iters"])
+            lo, hi = pt.band("bicgstab", r["entries"][tol])
+            assert lo <= e["max"] and hi >= e["min"], (r["case"], r["precond"], tol, r["entries"][tol], e["min"], e["max"])
