@@ -156,10 +156,11 @@ void gsk_opts_default(gsk_opts* opts);
  * it is read, so its values are read once and written once.
  * Accuracy: d_i is within a few ulp of the exact 1/||a_i||_p.  For FP64
  * values and p = 1 or 2, on rows whose largest magnitude lies within
- * 2^+-1000 (p = 1) or 2^+-480 (p = 2), the sum of |a_ij|^p is formed in
- * integer arithmetic on the aligned significands and rounded once (within
- * an ulp of the exact sum, whatever the order of the row's entries); other
- * rows are summed in FP64 after an exact power-of-two rescaling.
+ * 2^+-1000 (p = 1) or 2^+-480 (p = 2, rows of at most 4,095 entries), the
+ * sum of |a_ij|^p is formed in integer arithmetic on the aligned
+ * significands and rounded once (within an ulp of the exact sum, whatever
+ * the order of the row's entries); other rows are summed in FP64 after an
+ * exact power-of-two rescaling.
  * Errors: GSK_ERR_ARG (p < 1, bad sizes/pointers, row pointers out of
  * range), GSK_ERR_ZERO_ROW (a row is all zero, or its norm is below 2^-1024),
  * GSK_ERR_NONFINITE (NaN or Inf in a row or in b).  On error the rows that
