@@ -54,7 +54,7 @@ __device__ __forceinline__ bool finite_bits(double v) { return finite_pattern(db
 // are).  Tiles whose nonzeros exceed the staging capacity (very long rows)
 // are read straight from global memory.
 template <typename T, bool SCALE, int PM>
-__global__ void __launch_bounds__(kBlock) gs_rows_kernel(int n, int nnz, const int* __restrict__ rowptr,
+__global__ void __launch_bounds__(kBlock, 8) gs_rows_kernel(int n, int nnz, const int* __restrict__ rowptr,
                                                          T* __restrict__ val, T* __restrict__ b, double p,
                                                          double* __restrict__ d, int* err) {
   __shared__ T stage[kWarpsPerBlock][kStageCap];
